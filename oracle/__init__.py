@@ -1,0 +1,23 @@
+"""Plain, slow, complex128 CPU oracle for the CVS-ADC(2) hot path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg may import anything under ``oracle/``.  The
+product path (the C-ABI library and its Python binding) never imports,
+links or calls it, and shares no code with it.
+
+Modules:
+
+* ``integrals`` -- explicit antisymmetrised integrals from Cholesky vectors;
+* ``mp2``       -- MP2 doubles amplitudes, MP2 energy, MP2 vv density (Eq. 15);
+* ``fns``       -- frozen natural spinors (Eqs. 17-20) and B^P rotation;
+* ``adc2``      -- CVS spaces and packing, explicit CVS-ADC(2) blocks,
+                   matrix-free sigma, transition moments, eigen-solvers;
+* ``fci``       -- determinant-space engine and brute-force ISR, the
+                   independent pin of the ``adc2`` element formulas.
+
+Parity status of each function is stated in its docstring.  One gap is
+declared here: the second-order singles part of the modified transition
+moments, F^(2)_S, is not implemented; oscillator strengths are "through
+first order" (F^(0) + F^(1)), and both F^(0) and F^(1) are pinned by the
+brute-force ISR.
+"""

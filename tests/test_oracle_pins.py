@@ -1,0 +1,364 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test fixes the oracle to an independent source: the determinant-space
+Hamiltonian built from second-quantised operators, the brute-force ISR of
+section "Relativistic Algebraic Diagrammatic Construction Method",
+Rayleigh-Schrodinger perturbation theory, closed forms, and exact
+symmetries.  A dropped term, a wrong sign, a transposed operand or a wrong
+index anywhere in ``oracle.mp2`` / ``oracle.adc2`` / ``oracle.fns`` fails at
+least one of them.
+"""
+
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import adc2, fns, mp2
+from oracle.fci import DetSpace, ISR, apply_string, full_antisym_integrals
+from oracle.integrals import antisym
+from synth import make_instance, make_kramers_instance, make_spinfree_instance
+
+
+TINY = [dict(ncore=2, nval=2, nvirt=4, naux=6, seed=3, scale=0.15),
+        dict(ncore=2, nval=2, nvirt=5, naux=7, seed=11, scale=0.2)]
+
+
+@pytest.fixture(scope="module", params=range(len(TINY)))
+def tiny(request):
+    cfg = dict(TINY[request.param])
+    inst = make_instance(cfg["ncore"], cfg["nval"], cfg["nvirt"], cfg["naux"],
+                         seed=cfg["seed"], scale=cfg["scale"])
+    isr = ISR(inst.eps, inst.B, inst.ncore, inst.nval, inst.nvirt, dip=inst.dip)
+    cM, cF, cE = isr.taylor()
+    return inst, isr, cM, cF, cE
+
+
+# ---------------------------------------------------------------- T0 inputs
+
+def test_generator_deterministic_and_hermitian():
+    a = make_instance(3, 4, 6, 10, seed=5)
+    b = make_instance(3, 4, 6, 10, seed=5)
+    assert a.eps.tobytes() == b.eps.tobytes()
+    assert a.B.tobytes() == b.B.tobytes()
+    assert np.array_equal(a.B, np.conj(a.B.transpose(0, 2, 1)))
+    assert np.array_equal(a.dip, np.conj(a.dip.transpose(0, 2, 1)))
+    c = make_instance(3, 4, 6, 10, seed=6)
+    assert a.B.tobytes() != c.B.tobytes()
+    # Kramers-paired valence energies
+    assert np.all(a.eps[3:7:2] == a.eps[4:7:2])
+
+
+# ---------------------------------------------------- T1 determinant engine
+
+def test_fermion_anticommutators():
+    sp = DetSpace(5, 2)
+    # {a_p, a_q^+} = delta_pq on every 2-electron determinant, checked by
+    # applying a_p a_q^+ + a_q^+ a_p
+    for d in sp.dets:
+        for p in range(5):
+            for q in range(5):
+                acc = {}
+                for ops in ([(0, p), (1, q)], [(1, q), (0, p)]):
+                    r = apply_string(ops, d)
+                    if r is not None:
+                        acc[r[1]] = acc.get(r[1], 0) + r[0]
+                acc = {k: v for k, v in acc.items() if v != 0}
+                assert acc == ({d: 1} if p == q else {})
+
+
+def test_slater_condon_reference_elements():
+    inst = make_instance(2, 2, 3, 5, seed=2, scale=0.3)
+    isr = ISR(inst.eps, inst.B, 2, 2, 3)
+    sp, H = isr.space, isr.H
+    g = full_antisym_integrals(inst.B)
+    o = 4
+    ref = sp.index[sp.ref]
+    # E_HF = sum_i e_i - 1/2 sum_ij <ij||ij> for h = diag(e) - sum_k <pk||qk>
+    ehf = inst.eps[:o].sum() - 0.5 * sum(g[i, j, i, j] for i in range(o) for j in range(o))
+    assert abs(H[ref, ref] - ehf) < 1e-12
+    assert np.abs(H - H.conj().T).max() < 1e-13
+    for i in range(o):
+        for a in range(o, 7):
+            s, d = apply_string([(1, a), (0, i)], sp.ref)
+            # Brillouin: <Phi_i^a|H|Phi_0> = f_ai = 0
+            assert abs(H[sp.index[d], ref]) < 1e-13
+    for i, j in itertools.combinations(range(o), 2):
+        for a, b in itertools.combinations(range(o, 7), 2):
+            s, d = apply_string([(1, a), (1, b), (0, j), (0, i)], sp.ref)
+            assert abs(s * H[sp.index[d], ref] - g[a, b, i, j]) < 1e-13
+
+
+# ------------------------------------------------------------------ T2 MP2
+
+def test_mp2_energy_equals_rspt_and_fci_taylor(tiny):
+    inst, isr, cM, cF, cE = tiny
+    e2 = mp2.mp2_energy(inst.eps, inst.B, inst.ncore, inst.nval, inst.nvirt)
+    assert abs(e2.imag) < 1e-14
+    assert abs(e2.real - isr.rspt_e2()) < 1e-12 * abs(e2)
+    # second Taylor coefficient of the exact ground-state energy
+    assert abs(cE[2] - e2.real) < 1e-7 * abs(e2)
+    # zeroth + first order reproduce E_HF
+    assert abs(cE[0] + cE[1] - isr.e_hf) < 1e-9
+
+
+def test_mp2_cholesky_equals_full_integrals():
+    inst = make_instance(3, 4, 7, 12, seed=8)
+    nc, nw, nv = 3, 4, 7
+    o = nc + nw
+    g = full_antisym_integrals(inst.B)
+    e = inst.eps
+    full = 0.0
+    for i in range(o):
+        for j in range(o):
+            for a in range(o, o + nv):
+                for b in range(o, o + nv):
+                    full += 0.25 * abs(g[i, j, a, b]) ** 2 / (e[i] + e[j] - e[a] - e[b])
+    e2 = mp2.mp2_energy(e, inst.B, nc, nw, nv)
+    assert abs(e2 - full) < 1e-13 * abs(full)
+
+
+def test_t2_antisymmetry_and_density():
+    inst = make_instance(2, 4, 6, 9, seed=4)
+    t = mp2.t2_amplitudes(inst.eps, inst.B, 2, 4, 6)
+    tol = 1e-15 * np.abs(t).max()
+    assert np.abs(t + t.transpose(1, 0, 2, 3)).max() <= tol
+    assert np.abs(t + t.transpose(0, 1, 3, 2)).max() <= tol
+    D = mp2.density_vv(inst.eps, inst.B, 2, 4, 6)
+    assert np.abs(D - D.conj().T).max() < 1e-14 * np.abs(D).max()
+    w = np.linalg.eigvalsh(D)
+    assert w.min() > -1e-14 * w.max()
+    assert abs(np.trace(D) - 0.5 * np.sum(np.abs(t) ** 2)) < 1e-13 * abs(np.trace(D))
+
+
+# ------------------------------------------------------- T3 ISR brute force
+
+def _blocks(inst):
+    nc, nw, nv = inst.ncore, inst.nval, inst.nvirt
+    return (adc2.m11(inst.eps, inst.B, nc, nw, nv),
+            adc2.m11(inst.eps, inst.B, nc, nw, nv, second_order=False),
+            adc2.m21(inst.eps, inst.B, nc, nw, nv),
+            adc2.m22(inst.eps, nc, nw, nv))
+
+
+def test_isr_pins_m11_through_second_order(tiny):
+    inst, isr, cM, cF, cE = tiny
+    M11, M11_01, M21, d22 = _blocks(inst)
+    N1 = M11.shape[0]
+    ref2 = cM[0][:N1, :N1] + cM[1][:N1, :N1] + cM[2][:N1, :N1]
+    ref1 = cM[0][:N1, :N1] + cM[1][:N1, :N1]
+    scale = np.abs(ref2).max()
+    assert np.abs(M11_01 - ref1).max() < 1e-10 * scale
+    second = M11 - M11_01
+    assert np.abs(second).max() > 1e-3 * scale  # the second order term matters
+    assert np.abs(M11 - ref2).max() < 1e-7 * scale
+
+
+def test_isr_pins_coupling_and_doubles(tiny):
+    inst, isr, cM, cF, cE = tiny
+    M11, M11_01, M21, d22 = _blocks(inst)
+    N1 = M11.shape[0]
+    assert np.abs(cM[0][N1:, :N1]).max() < 1e-12
+    assert np.abs(M21 - cM[1][N1:, :N1]).max() < 1e-9 * np.abs(M21).max()
+    assert np.abs(cM[0][N1:, N1:] - np.diag(d22)).max() < 1e-10 * np.abs(d22).max()
+
+
+def test_isr_pins_transition_moments(tiny):
+    inst, isr, cM, cF, cE = tiny
+    F = adc2.transition_moments(inst.eps, inst.B, inst.dip, inst.ncore,
+                                inst.nval, inst.nvirt)
+    ref = cF[0] + cF[1]
+    assert np.abs(F - ref).max() < 1e-9 * np.abs(ref).max()
+    # the first-order part is non-trivial
+    assert np.abs(cF[1]).max() > 1e-3 * np.abs(cF[0]).max()
+
+
+# ------------------------------------------------ T4 Hermiticity and sigma
+
+def test_hermitian_and_sigma_equals_dense():
+    inst = make_instance(3, 4, 7, 12, seed=21)
+    nc, nw, nv = 3, 4, 7
+    M = adc2.adc_matrix(inst.eps, inst.B, nc, nw, nv)
+    assert np.abs(M - M.conj().T).max() < 1e-13 * np.abs(M).max()
+    sig = adc2.Sigma(inst.eps, inst.B, nc, nw, nv)
+    rng = np.random.default_rng(0)
+    N1, _, N2 = adc2.sizes(nc, nw, nv)
+    x = rng.standard_normal(N1 + N2) + 1j * rng.standard_normal(N1 + N2)
+    s1, s2 = sig(x[:N1], x[N1:])
+    ref = M @ x
+    assert np.abs(np.concatenate([s1, s2]) - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------ T5 CIS limit
+
+def test_cis_limit_from_determinants():
+    inst = make_instance(2, 3, 5, 8, seed=9, scale=0.4)
+    nc, nw, nv = 2, 3, 5
+    isr = ISR(inst.eps, inst.B, nc, nw, nv)
+    sp, H = isr.space, isr.H
+    ref = sp.index[sp.ref]
+    o = nc + nw
+    rows = []
+    for I in range(nc):
+        for a in range(nv):
+            s, d = apply_string([(1, o + a), (0, I)], sp.ref)
+            rows.append((sp.index[d], s))
+    idx = np.array([r[0] for r in rows])
+    sg = np.array([r[1] for r in rows], dtype=float)
+    cis = (sg[:, None] * sg[None, :]) * H[np.ix_(idx, idx)] - H[ref, ref] * np.eye(len(rows))
+    M = adc2.adc_matrix(inst.eps, inst.B, nc, nw, nv, second_order=False)
+    w_adc = np.linalg.eigvalsh(M)[: nc * nv]
+    # with the second order switched off the core-singles block decouples;
+    # its eigenvalues are those of the CIS matrix over core singles
+    M11 = adc2.m11(inst.eps, inst.B, nc, nw, nv, second_order=False)
+    assert np.abs(M11 - cis).max() < 1e-12 * np.abs(cis).max()
+    w_cis = np.linalg.eigvalsh(cis)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(M11)), w_cis, atol=1e-11)
+    assert w_adc.min() <= w_cis.min() + 1e-9  # doubles only add states
+
+
+# ---------------------------------------------------- T6 symmetry pins
+
+def _tr_map(nc, nw, nv):
+    """Time reversal on the packed CVS basis: basis vector P maps to
+    eta_P * basis vector tau(P)."""
+    o = nc + nw
+    s = lambda p: 1 if p % 2 == 0 else -1  # noqa: E731
+    perm, eta = [], []
+    for I in range(nc):
+        for a in range(nv):
+            perm.append((I ^ 1) * nv + (a ^ 1))
+            eta.append(s(I) * s(o + a))
+    npair = nv * (nv - 1) // 2
+    pos = {tuple(p): k for k, p in enumerate(adc2.pair_list(nv).tolist())}
+    N1 = nc * nv
+    for I in range(nc):
+        for j in range(nw):
+            for a, b in itertools.combinations(range(nv), 2):
+                ta, tb = a ^ 1, b ^ 1
+                sg = s(I) * s(nc + j) * s(o + a) * s(o + b)
+                if ta > tb:
+                    ta, tb = tb, ta
+                    sg = -sg
+                perm.append(N1 + ((I ^ 1) * nw + ((nc + j) ^ 1) - nc) * npair + pos[(ta, tb)])
+                eta.append(sg)
+    return np.array(perm), np.array(eta, dtype=float)
+
+
+def test_time_reversal_covariance():
+    inst = make_kramers_instance(2, 2, 6, 8, seed=13)
+    nc, nw, nv = 2, 2, 6
+    M = adc2.adc_matrix(inst.eps, inst.B, nc, nw, nv)
+    perm, eta = _tr_map(nc, nw, nv)
+    lhs = M[np.ix_(perm, perm)]
+    rhs = eta[:, None] * eta[None, :] * np.conj(M)
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(M).max()
+    # the same map on a generic instance fails: the test has teeth
+    gen = make_instance(2, 2, 6, 8, seed=13)
+    Mg = adc2.adc_matrix(gen.eps, gen.B, nc, nw, nv)
+    assert np.abs(Mg[np.ix_(perm, perm)] - eta[:, None] * eta[None, :] * np.conj(Mg)).max() > 1e-3
+
+
+def test_spin_free_triplets_threefold():
+    inst = make_spinfree_instance(2, 2, 6, 8, seed=17, scale=0.2)
+    M = adc2.adc_matrix(inst.eps, inst.B, 2, 2, 6)
+    w = np.linalg.eigvalsh(M)
+    clusters, start = [], 0
+    for k in range(1, len(w) + 1):
+        if k == len(w) or w[k] - w[k - 1] > 1e-8:
+            clusters.append(k - start)
+            start = k
+    # singlets, triplets and (two holes + two particles) quintets only
+    assert set(clusters) <= {1, 3, 5}, clusters
+    assert 3 in clusters and 1 in clusters
+    # a generic (spin-orbit coupled) instance has no such multiplets
+    gen = make_instance(2, 2, 6, 8, seed=17, scale=0.2)
+    wg = np.linalg.eigvalsh(adc2.adc_matrix(gen.eps, gen.B, 2, 2, 6))
+    assert np.min(np.diff(wg)) > 1e-7
+
+
+# ------------------------------------------------------------------ T7 FNS
+
+def test_fns_keep_all_is_exact_invariance():
+    inst = make_instance(2, 3, 8, 10, seed=31)
+    nc, nw, nv = 2, 3, 8
+    n, U, et = fns.natural_spinors(inst.eps, inst.B, nc, nw, nv, tau=-1.0)
+    assert U.shape == (nv, nv)
+    assert np.abs(U.conj().T @ U - np.eye(nv)).max() < 1e-13
+    D = mp2.density_vv(inst.eps, inst.B, nc, nw, nv)
+    assert abs(n.sum() - np.trace(D).real) < 1e-14 * abs(n.sum())
+    assert n.min() > -1e-15
+    e2, B2 = fns.rotate(inst.eps, inst.B, nc, nw, nv, U, et)
+    w0 = np.linalg.eigvalsh(adc2.adc_matrix(inst.eps, inst.B, nc, nw, nv))[:6]
+    w1 = np.linalg.eigvalsh(adc2.adc_matrix(e2, B2, nc, nw, nv))[:6]
+    assert np.abs(w0 - w1).max() < 1e-10
+    # semicanonical: F stays diagonal, energies are the sorted originals
+    assert np.allclose(np.sort(et), np.sort(inst.eps[nc + nw:]), atol=1e-13)
+
+
+def test_fns_truncation_counts_and_rotation():
+    inst = make_instance(2, 3, 10, 10, seed=32, scale=0.1)
+    nc, nw, nv = 2, 3, 10
+    D = mp2.density_vv(inst.eps, inst.B, nc, nw, nv)
+    occ = np.sort(np.linalg.eigvalsh(D))[::-1]
+    tau = 0.5 * (occ[4] + occ[5])
+    n, U, et = fns.natural_spinors(inst.eps, inst.B, nc, nw, nv, tau)
+    assert U.shape == (nv, 5)
+    assert np.abs(U.conj().T @ U - np.eye(5)).max() < 1e-13
+    e2, B2 = fns.rotate(inst.eps, inst.B, nc, nw, nv, U, et)
+    o = nc + nw
+    # rotated Fock block is diagonal with eps~
+    F = U.conj().T @ np.diag(inst.eps[o:]) @ U
+    assert np.abs(F - np.diag(et)).max() < 1e-13
+    # rotated vectors are still Hermitian
+    assert np.abs(B2 - np.conj(B2.transpose(0, 2, 1))).max() < 1e-14
+
+
+# ------------------------------------------------------------ T8 solvers
+
+def test_dense_partitioned_lanczos_agree():
+    inst = make_instance(2, 4, 12, 16, seed=41)
+    nc, nw, nv = 2, 4, 12
+    M11 = adc2.m11(inst.eps, inst.B, nc, nw, nv)
+    M21 = adc2.m21(inst.eps, inst.B, nc, nw, nv)
+    d22 = adc2.m22(inst.eps, nc, nw, nv)
+    M = np.block([[M11, M21.conj().T], [M21, np.diag(d22).astype(complex)]])
+    wd, Xd = adc2.eig_dense(M, 4)
+    wp, Xp = adc2.eig_partitioned(M11, M21, d22, 4)
+    wl, Xl = adc2.eig_lanczos(M11, M21, d22, 4)
+    assert np.abs(wd - wp).max() < 1e-10 * max(1, abs(wd).max())
+    assert np.abs(wd - wl).max() < 1e-9 * max(1, abs(wd).max())
+    for k in range(4):
+        assert abs(abs(np.vdot(Xd[k], Xp[k])) - 1) < 1e-8
+        assert np.linalg.norm(M @ Xp[k] - wp[k] * Xp[k]) < 1e-9 * abs(wp[k])
+
+
+# ------------------------------------------------------------ T9 packing
+
+def test_packing_bit_exact():
+    for nc, nw, nv in [(2, 3, 5), (6, 14, 40), (1, 1, 2)]:
+        tab = adc2.doubles_list(nc, nw, nv)
+        N1, npair, N2 = adc2.sizes(nc, nw, nv)
+        assert tab.shape == (N2, 4)
+        I, j, a, b = tab.T
+        pair = a * (2 * nv - a - 1) // 2 + (b - a - 1)
+        d = (I * nw + j) * npair + pair
+        assert np.array_equal(d, np.arange(N2, dtype=np.int64))
+        rng = np.random.default_rng(1)
+        x = rng.standard_normal(N2) + 1j * rng.standard_normal(N2)
+        assert np.array_equal(adc2.pack(adc2.unpack(x, nc, nw, nv), nv), x)
+
+
+# ------------------------------------------------ transition moment algebra
+
+def test_oscillator_linearity_and_phase():
+    inst = make_instance(2, 2, 6, 8, seed=5)
+    nc, nw, nv = 2, 2, 6
+    M = adc2.adc_matrix(inst.eps, inst.B, nc, nw, nv)
+    w, X = adc2.eig_dense(M, 3)
+    F = adc2.transition_moments(inst.eps, inst.B, inst.dip, nc, nw, nv)
+    f = adc2.oscillator_strengths(w, X, F)
+    F2 = adc2.transition_moments(inst.eps, inst.B, 2.5 * inst.dip, nc, nw, nv)
+    assert np.allclose(adc2.oscillator_strengths(w, X, F2), 6.25 * f, rtol=1e-13)
+    ph = np.exp(1j * np.array([0.3, -1.2, 2.0]))[:, None]
+    assert np.allclose(adc2.oscillator_strengths(w, X * ph, F), f, rtol=1e-13)
