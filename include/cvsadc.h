@@ -1,0 +1,189 @@
+/*
+ * cvsadc.h -- C ABI of libcvsadc, a GB300 (sm_103a) implementation of the
+ * hot path of Cholesky-decomposed two-component CVS-ADC(2) for L-edge core
+ * excitations over complex spinors (arXiv 2604.27451).
+ *
+ * Problem statement (section "Implementation and Computational Details"
+ * and section "Core-Valence Separation (CVS)"): spinor energies, complex
+ * Cholesky vectors B^P_pq, the core / valence / virtual partition and the
+ * dipole matrices go in; the lowest CVS-ADC(2) excitation energies
+ * (Eq. 11, M X = X Omega), their eigenvectors and oscillator strengths
+ * (f = 2/3 omega |T|^2, section "Properties in ISR formulation") come out.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Spinor order: [core | valence | virtual], n = ncore + nval + nvirt.
+ *   Frozen core is already removed: every occupied spinor is correlated.
+ * Complex numbers: interleaved (re, im) double pairs, i.e. C99 double
+ *   complex / numpy complex128 layout.
+ * eps : [n] double, canonical spinor energies (Fock matrix = diag(eps)).
+ * B   : [naux][n][n] complex, row-major, B[P][p][q] = B^P_pq; every B^P
+ *   must be Hermitian (B^P_pq = conj(B^P_qp)); two-electron integrals are
+ *   (pq|rs) = sum_P B^P_pq B^P_rs and <pq||rs> = (pr|qs) - (ps|qr).
+ * dip : [3][n][n] complex, each Hermitian; d_pq = <p|mu_x|q>.
+ * CVS packed vectors (length N = N1 + N2):
+ *   singles s = I*nvirt + a                              (N1 = ncore*nvirt)
+ *   doubles N1 + (I*nval + j)*npair + pair(a,b), a < b  (npair = nvirt(nvirt-1)/2,
+ *     pair(a,b) = a*(2*nvirt-a-1)/2 + (b-a-1),          N2 = ncore*nval*npair)
+ *   basis vectors a_a^+ a_I |Phi0> and a_a^+ a_b^+ a_I a_j |Phi0>, the
+ *   operator order of the CVS section.
+ * Ownership: the caller owns every buffer it passes; the library copies or
+ *   reads inputs and writes outputs, and never keeps a caller pointer after
+ *   a call returns.  The context owns its device workspaces.
+ * Memory space: pointers are host memory unless CVSADC_FLAG_DEVICE_PTRS is
+ *   set in params->flags, in which case every array argument of that call
+ *   is device memory on the context's device.
+ * Errors: every int-returning function returns CVSADC_OK (0) on success, a
+ *   negative code on failure (nothing is written to outputs except where
+ *   stated), or CVSADC_ENOTCONV (> 0) when the eigen-solver hit max_iter
+ *   (outputs then hold the best estimate).  No exception crosses the ABI.
+ * Threads/streams: one context per host thread; all work is issued on the
+ *   context's stream and every call returns after that stream is synchronised.
+ * Units: Hartree.
+ */
+#ifndef CVSADC_H
+#define CVSADC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define CVSADC_OK 0
+#define CVSADC_EINVAL (-1)     /* bad sizes, partition or argument */
+#define CVSADC_ENONHERM (-2)   /* B^P or a dipole matrix not Hermitian */
+#define CVSADC_ENOMEM (-3)     /* device allocation failed */
+#define CVSADC_ECUDA (-4)      /* CUDA runtime/driver error */
+#define CVSADC_ETIMEOUT (-5)   /* a bounded device wait gave up */
+#define CVSADC_ESTATE (-6)     /* call order: no prepared problem */
+#define CVSADC_ENOTCONV 1      /* max_iter reached, best estimate returned */
+
+/* ----------------------------------------------------------- precision */
+#define CVSADC_FP64 0          /* complex128 throughout, FP64 FMA GEMMs */
+#define CVSADC_MIXED_BF16X3 1  /* GEMMs on tcgen05 tensor cores with
+                                  3-term bf16 splits and FP32 accumulation;
+                                  denominators, Gram-Schmidt, norms,
+                                  subspace eigensolve and the final residual
+                                  correction in FP64 */
+
+/* ---------------------------------------------------------------- flags */
+#define CVSADC_FLAG_DEVICE_PTRS 1  /* array arguments are device pointers */
+#define CVSADC_FLAG_RETURN_X 2     /* write eigenvectors to X */
+#define CVSADC_FLAG_NO_REFINE 4    /* mixed path: skip the FP64 residual
+                                      correction sweep */
+
+typedef struct {
+  int32_t ncore, nval, nvirt, naux;
+  int32_t nroots;         /* lowest nroots eigenvalues of the CVS-ADC(2) matrix */
+  int32_t precision;      /* CVSADC_FP64 or CVSADC_MIXED_BF16X3 */
+  double fns_threshold;   /* tau for frozen natural spinors; <= 0 keeps all virtuals */
+  double conv_residual;   /* Davidson convergence, 2-norm of M x - w x; default 1e-6 */
+  int32_t max_iter;       /* default 400: roots dominated by strongly coupled
+                             doubles can take a few hundred iterations */
+  int32_t max_subspace;   /* default max(8 nroots, 48) */
+  int32_t flags;          /* CVSADC_FLAG_* */
+  int32_t reserved;
+} cvsadc_params;
+
+typedef struct {
+  int32_t iterations;      /* Davidson iterations */
+  int32_t sigma_vectors;   /* single-vector sigma builds done */
+  int32_t nvirt_kept;      /* virtuals after FNS truncation */
+  int32_t converged;       /* number of converged roots */
+  double emp2;             /* MP2 correlation energy (final basis) */
+  double max_residual;     /* max over roots of ||M x - w x|| */
+  double t_prepare_ms;     /* t2 + FNS + M11 + transition moments */
+  double t_davidson_ms;    /* Davidson iterations */
+  double t_refine_ms;      /* FP64 residual correction */
+  double t_total_ms;
+} cvsadc_info;
+
+typedef struct cvsadc_ctx cvsadc_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t (NULL: the context creates its own non-blocking stream).
+ * Returns CVSADC_EINVAL for a bad device, CVSADC_ECUDA on runtime errors. */
+int cvsadc_create(cvsadc_ctx** ctx, int device, void* cuda_stream);
+
+/* Release every device buffer and the context.  NULL is accepted. */
+void cvsadc_destroy(cvsadc_ctx* ctx);
+
+/* Human-readable text for a status code (static storage). */
+const char* cvsadc_strerror(int status);
+
+/* Text of the last error recorded on ctx (static per context). */
+const char* cvsadc_last_error(cvsadc_ctx* ctx);
+
+/* --------------------------------------------------------------------
+ * cvsadc_solve -- the whole path in one call.
+ * Section "Implementation and Computational Details": MP2 amplitudes from
+ * the Cholesky vectors, optional frozen-natural-spinor truncation (Eqs.
+ * 15, 17-20) with rotation of B^P, the CVS-ADC(2) matrix (Eqs. 11-12 under
+ * the CVS restriction), a Davidson eigensolver, and transition moments
+ * through first order with oscillator strengths.
+ *   omega : [nroots] out, ascending excitation energies (Eh)
+ *   X     : [nroots][N] complex out (CVS packed, in the final basis) or NULL;
+ *           written only with CVSADC_FLAG_RETURN_X.  The largest-modulus
+ *           component of each vector is made real and positive.
+ *   osc   : [nroots] out or NULL (requires dip)
+ *   dip   : may be NULL (no oscillator strengths)
+ *   info  : may be NULL
+ * Errors: EINVAL (sizes, nroots > N, NULL required pointer), ENONHERM
+ * (B or dip not Hermitian to 1e-12 of its largest entry), ENOMEM, ECUDA.
+ */
+int cvsadc_solve(cvsadc_ctx* ctx, const cvsadc_params* params,
+                 const double* eps, const void* B, const void* dip,
+                 double* omega, void* X, double* osc, cvsadc_info* info);
+
+/* --------------------------------------------------------------------
+ * Stage entry points.  cvsadc_prepare runs everything before the
+ * eigen-solver and keeps the result in ctx; the calls below it then use
+ * that prepared problem (CVSADC_ESTATE if there is none).
+ */
+
+/* MP2 amplitudes, MP2 energy and (if tau > 0) the FNS truncation with the
+ * rotation of B^P, then the M11 block and the transition moments.  The
+ * dipole pointer may be NULL.  Section "Implementation and Computational
+ * Details", Eqs. 15 and 17-20. */
+int cvsadc_prepare(cvsadc_ctx* ctx, const cvsadc_params* params,
+                   const double* eps, const void* B, const void* dip,
+                   cvsadc_info* info);
+
+/* Sizes of the prepared problem: nvirt after truncation, N1, N2. */
+int cvsadc_prepared_sizes(cvsadc_ctx* ctx, int32_t* nvirt, int64_t* N1,
+                          int64_t* N2);
+
+/* MP2 amplitudes of the prepared problem, t[i][j][a][b] = t^{ab}_{ij} =
+ * <ab||ij>/(e_i+e_j-e_a-e_b), [o][o][v][v] complex (o = ncore+nval, v =
+ * nvirt after truncation), and E_MP2 = 1/4 sum <ij||ab> t^{ab}_{ij}.
+ * t2 may be NULL.  Memory space per `flags` (CVSADC_FLAG_DEVICE_PTRS). */
+int cvsadc_get_t2(cvsadc_ctx* ctx, int32_t flags, void* t2, double* emp2);
+
+/* The explicit core-singles block M11 [N1][N1] complex (row-major). */
+int cvsadc_get_m11(cvsadc_ctx* ctx, int32_t flags, void* m11);
+
+/* FNS results of the prepared problem: occupations [nvirt_in] (descending)
+ * and U [nvirt_in][nvirt_kept] complex; either may be NULL.  Only valid
+ * when the problem was prepared with tau > 0. */
+int cvsadc_get_fns(cvsadc_ctx* ctx, int32_t flags, double* occ, void* U);
+
+/* Modified transition moments F [3][N] complex, through first order. */
+int cvsadc_get_moments(cvsadc_ctx* ctx, int32_t flags, void* F);
+
+/* sigma = M x for nvec CVS-packed vectors x [nvec][N] complex, written to
+ * sigma [nvec][N].  precision: CVSADC_FP64 or CVSADC_MIXED_BF16X3 (the
+ * couplings M12 and M21 are contracted through B^P; M22 is applied on the
+ * fly; M11 x1 is a dense product). */
+int cvsadc_sigma(cvsadc_ctx* ctx, int32_t precision, int32_t flags,
+                 const void* x, void* sigma, int32_t nvec);
+
+/* Davidson on the prepared problem (see cvsadc_solve for outputs). */
+int cvsadc_davidson(cvsadc_ctx* ctx, const cvsadc_params* params,
+                    double* omega, void* X, double* osc, cvsadc_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CVSADC_H */

@@ -1,0 +1,224 @@
+"""GB300 (sm_103a) CVS-ADC(2) hot path: Python front end of libcvsadc.
+
+The package is a thin layer over the C ABI of ``include/cvsadc.h``: it
+marshals numpy arrays (host memory) or torch CUDA tensors (device memory)
+into the library calls.  All arithmetic runs in the library's CUDA
+kernels; importing :class:`Context` fails loudly when the library is not
+built.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    CVSADC_FLAG_DEVICE_PTRS, CVSADC_FLAG_NO_REFINE, CVSADC_FLAG_RETURN_X,
+    CVSADC_FP64, CVSADC_MIXED_BF16X3, CVSADC_ENOTCONV, Info, Params,
+)
+
+PRECISIONS = {"fp64": CVSADC_FP64, "bf16x3": CVSADC_MIXED_BF16X3,
+              "mixed": CVSADC_MIXED_BF16X3}
+
+
+class CvsadcError(RuntimeError):
+    def __init__(self, code, text):
+        super().__init__("cvsadc error %d: %s" % (code, text))
+        self.code = code
+
+
+def _is_torch_cuda(x):
+    return hasattr(x, "is_cuda") and hasattr(x, "data_ptr") and x.is_cuda
+
+
+def _ptr(x):
+    """(pointer, is_device) of a numpy array or torch CUDA tensor."""
+    if x is None:
+        return None, None
+    if _is_torch_cuda(x):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), True
+    if not isinstance(x, np.ndarray) or not x.flags.c_contiguous:
+        raise ValueError("host arrays must be C-contiguous numpy arrays")
+    return ctypes.c_void_p(x.ctypes.data), False
+
+
+class Context:
+    """One libcvsadc context (one device, one stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = _lib.load()
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(int(stream)) if stream else None
+        rc = self.lib.cvsadc_create(ctypes.byref(h), device, s)
+        if rc != 0:
+            raise CvsadcError(rc, self.lib.cvsadc_strerror(rc).decode())
+        self.h = h
+        self._shape = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.cvsadc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow_notconv=False):
+        if rc == 0 or (allow_notconv and rc == CVSADC_ENOTCONV):
+            return rc
+        msg = self.lib.cvsadc_last_error(self.h).decode() or \
+            self.lib.cvsadc_strerror(rc).decode()
+        raise CvsadcError(rc, msg)
+
+    # ------------------------------------------------------------ params
+    @staticmethod
+    def params(ncore, nval, nvirt, naux, nroots=4, precision="fp64",
+               tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, flags=0):
+        p = Params()
+        p.ncore, p.nval, p.nvirt, p.naux = ncore, nval, nvirt, naux
+        p.nroots = nroots
+        p.precision = PRECISIONS[precision] if isinstance(precision, str) else precision
+        p.fns_threshold = tau
+        p.conv_residual = conv
+        p.max_iter = max_iter
+        p.max_subspace = max_subspace
+        p.flags = flags
+        return p
+
+    # ----------------------------------------------------------- stages
+    def prepare(self, eps, B, dip=None, ncore=None, nval=None, nvirt=None,
+                precision="fp64", tau=0.0):
+        naux = B.shape[0]
+        pe, dev = _ptr(eps)
+        pb, _ = _ptr(B)
+        pd, _ = _ptr(dip)
+        p = self.params(ncore, nval, nvirt, naux, 1, precision, tau,
+                        flags=CVSADC_FLAG_DEVICE_PTRS if dev else 0)
+        info = Info()
+        self._check(self.lib.cvsadc_prepare(self.h, ctypes.byref(p), pe, pb, pd,
+                                            ctypes.byref(info)))
+        nv = ctypes.c_int32()
+        n1 = ctypes.c_int64()
+        n2 = ctypes.c_int64()
+        self._check(self.lib.cvsadc_prepared_sizes(self.h, ctypes.byref(nv),
+                                                   ctypes.byref(n1), ctypes.byref(n2)))
+        self._shape = dict(ncore=ncore, nval=nval, nvirt_in=nvirt, nvirt=nv.value,
+                           naux=naux, N1=n1.value, N2=n2.value, N=n1.value + n2.value)
+        return info.as_dict()
+
+    @property
+    def shape(self):
+        return self._shape
+
+    def get_t2(self):
+        s = self._shape
+        o = s["ncore"] + s["nval"]
+        v = s["nvirt"]
+        t2 = np.empty((o, o, v, v), dtype=np.complex128)
+        e = ctypes.c_double()
+        self._check(self.lib.cvsadc_get_t2(self.h, 0, ctypes.c_void_p(t2.ctypes.data),
+                                           ctypes.byref(e)))
+        return t2, e.value
+
+    def get_m11(self):
+        n1 = self._shape["N1"]
+        m = np.empty((n1, n1), dtype=np.complex128)
+        self._check(self.lib.cvsadc_get_m11(self.h, 0, ctypes.c_void_p(m.ctypes.data)))
+        return m
+
+    def get_moments(self):
+        F = np.empty((3, self._shape["N"]), dtype=np.complex128)
+        self._check(self.lib.cvsadc_get_moments(self.h, 0, ctypes.c_void_p(F.ctypes.data)))
+        return F
+
+    def get_fns(self):
+        s = self._shape
+        occ = np.empty(s["nvirt_in"], dtype=np.float64)
+        U = np.empty((s["nvirt_in"], s["nvirt"]), dtype=np.complex128)
+        self._check(self.lib.cvsadc_get_fns(self.h, 0, ctypes.c_void_p(occ.ctypes.data),
+                                            ctypes.c_void_p(U.ctypes.data)))
+        return occ, U
+
+    def sigma(self, x, precision="fp64", out=None):
+        """sigma = M x for x [nvec][N] (numpy host or torch CUDA)."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        nvec = x.shape[0] if x.ndim == 2 else 1
+        px, dev = _ptr(x)
+        if out is None:
+            if dev:
+                import torch
+                out = torch.empty_like(x)
+            else:
+                out = np.empty_like(x)
+        po, _ = _ptr(out)
+        flags = CVSADC_FLAG_DEVICE_PTRS if dev else 0
+        self._check(self.lib.cvsadc_sigma(self.h, prec, flags, px, po, nvec))
+        return out
+
+    def davidson(self, nroots, precision="fp64", conv=1e-6, max_iter=0,
+                 max_subspace=0, return_x=False, refine=True):
+        s = self._shape
+        flags = (CVSADC_FLAG_RETURN_X if return_x else 0) | \
+            (0 if refine else CVSADC_FLAG_NO_REFINE)
+        p = self.params(s["ncore"], s["nval"], s["nvirt"], s["naux"], nroots,
+                        precision, 0.0, conv, max_iter, max_subspace, flags)
+        omega = np.empty(nroots)
+        osc = np.empty(nroots)
+        X = np.empty((nroots, s["N"]), dtype=np.complex128) if return_x else None
+        info = Info()
+        rc = self.lib.cvsadc_davidson(
+            self.h, ctypes.byref(p), ctypes.c_void_p(omega.ctypes.data),
+            ctypes.c_void_p(X.ctypes.data) if X is not None else None,
+            ctypes.c_void_p(osc.ctypes.data), ctypes.byref(info))
+        self._check(rc, allow_notconv=True)
+        return dict(omega=omega, osc=osc, X=X, info=info.as_dict(), status=rc)
+
+    def solve(self, eps, B, dip, ncore, nval, nvirt, nroots, precision="fp64",
+              tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, return_x=False):
+        """The whole path through cvsadc_solve."""
+        naux = B.shape[0]
+        pe, dev = _ptr(eps)
+        pb, _ = _ptr(B)
+        pd, _ = _ptr(dip)
+        flags = (CVSADC_FLAG_DEVICE_PTRS if dev else 0) | \
+            (CVSADC_FLAG_RETURN_X if return_x else 0)
+        p = self.params(ncore, nval, nvirt, naux, nroots, precision, tau, conv,
+                        max_iter, max_subspace, flags)
+        if dev:
+            import torch
+            omega = torch.empty(nroots, dtype=torch.float64, device=eps.device)
+            osc = torch.empty(nroots, dtype=torch.float64, device=eps.device)
+        else:
+            omega = np.empty(nroots)
+            osc = np.empty(nroots)
+        X = None
+        if return_x:
+            # the size after FNS truncation is known only after the call;
+            # the untruncated space bounds it
+            nv = nvirt
+            N = ncore * nv + ncore * nval * nv * (nv - 1) // 2
+            X = np.zeros(nroots * N, dtype=np.complex128)
+        info = Info()
+        rc = self.lib.cvsadc_solve(
+            self.h, ctypes.byref(p), pe, pb, pd, _ptr(omega)[0],
+            ctypes.c_void_p(X.ctypes.data) if X is not None else None,
+            _ptr(osc)[0] if dip is not None else None, ctypes.byref(info))
+        self._check(rc, allow_notconv=True)
+        nv = ctypes.c_int32()
+        n1 = ctypes.c_int64()
+        n2 = ctypes.c_int64()
+        self._check(self.lib.cvsadc_prepared_sizes(self.h, ctypes.byref(nv),
+                                                   ctypes.byref(n1), ctypes.byref(n2)))
+        self._shape = dict(ncore=ncore, nval=nval, nvirt_in=nvirt, nvirt=nv.value,
+                           naux=naux, N1=n1.value, N2=n2.value, N=n1.value + n2.value)
+        if X is not None:
+            X = X[: nroots * self._shape["N"]].reshape(nroots, self._shape["N"])
+        return dict(omega=omega, osc=osc if dip is not None else None, X=X,
+                    info=info.as_dict(), status=rc)

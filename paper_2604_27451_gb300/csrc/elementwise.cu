@@ -1,0 +1,788 @@
+// Bandwidth-bound kernels of the CVS-ADC(2) path: Hermiticity check, the
+// t2 epilogue with the MP2 energy, M11 assembly, the CVS pack/unpack with
+// the on-the-fly M22, and the Davidson vector kernels.
+#include "common.cuh"
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace cvs {
+
+namespace {
+
+__device__ __forceinline__ int64_t pair_index(int a, int b, int v) {
+  // a < b; pair(a,b) = a(2v-a-1)/2 + (b-a-1)
+  return (int64_t)a * (2 * v - a - 1) / 2 + (b - a - 1);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block-wide sum of one double, result valid in thread 0
+__device__ double block_sum(double v) {
+  __shared__ double red[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? red[threadIdx.x] : 0.0;
+  if (wid == 0) v = warp_sum(v);
+  return v;
+}
+
+__global__ void scale_view_kernel(int M, int N, double beta, View C) {
+  int64_t total = (int64_t)M * N;
+  cplx* p = C.p + (int64_t)blockIdx.y * C.batch;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int r = idx / N, c = idx % N;
+    cplx* d = p + vrow(C, r) + vcol(C, c);
+    *d = beta == 0.0 ? cmake(0, 0) : cscale(*d, beta);
+  }
+}
+
+__global__ void herm_kernel(const cplx* B, int n, int64_t nmat, double* out) {
+  int64_t total = nmat * n * (int64_t)n;
+  double dev = 0.0, mx = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t P = idx / ((int64_t)n * n);
+    int64_t rem = idx - P * n * (int64_t)n;
+    int p = rem / n, q = rem % n;
+    cplx a = B[idx];
+    cplx b = B[P * n * (int64_t)n + (int64_t)q * n + p];
+    double d = hypot(a.x - b.x, a.y + b.y);
+    dev = fmax(dev, d);
+    mx = fmax(mx, hypot(a.x, a.y));
+  }
+  // block max via shared memory
+  __shared__ double s0[256], s1[256];
+  s0[threadIdx.x] = dev;
+  s1[threadIdx.x] = mx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s0[threadIdx.x] = fmax(s0[threadIdx.x], s0[threadIdx.x + o]);
+      s1[threadIdx.x] = fmax(s1[threadIdx.x], s1[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // non-negative doubles order like their bit patterns
+    atomicMax((unsigned long long*)&out[0], __double_as_longlong(s0[0]));
+    atomicMax((unsigned long long*)&out[1], __double_as_longlong(s1[0]));
+  }
+}
+
+__global__ void t2_band_kernel(const cplx* __restrict__ V, int a0, int na,
+                               int o, int v, const double* __restrict__ eps,
+                               cplx* __restrict__ t2, cplx* __restrict__ g2,
+                               double* part) {
+  const int64_t ldV = (int64_t)v * o;
+  const int64_t total = (int64_t)na * o * o * v;
+  double acc = 0.0;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int b = idx % v;
+    int64_t r = idx / v;
+    int j = r % o;
+    r /= o;
+    int i = r % o;
+    int al = r / o;
+    int a = a0 + al;
+    cplx v1 = V[((int64_t)al * o + i) * ldV + (int64_t)b * o + j];
+    cplx v2 = V[((int64_t)al * o + j) * ldV + (int64_t)b * o + i];
+    cplx g = csub(v1, v2);
+    double den = eps[i] + eps[j] - eps[o + a] - eps[o + b];
+    int64_t dst = (((int64_t)i * o + j) * v + a) * v + b;
+    g2[dst] = g;
+    t2[dst] = cscale(g, 1.0 / den);
+    acc += 0.25 * (g.x * g.x + g.y * g.y) / den;
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] += s;
+}
+
+__global__ void reduce_sum_kernel(const double* in, int n, double* out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += in[i];
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void m11_kernel(int nc, int nv, int o, const double* eps,
+                           const cplx* C1, const cplx* C2, const cplx* X,
+                           const cplx* Y, const cplx* Z, int second,
+                           cplx* M11) {
+  const int64_t N1 = (int64_t)nc * nv;
+  const int64_t total = N1 * N1;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t row = idx / N1, col = idx % N1;
+    int I = row / nv, a = row % nv, J = col / nv, b = col % nv;
+    cplx val = cmake(0, 0);
+    if (I == J && a == b) val.x = eps[o + a] - eps[I];
+    // <aJ||bI> = (ab|JI) - (aI|Jb)
+    cplx c1 = C1[((int64_t)a * nv + b) * (nc * nc) + J * nc + I];
+    cplx c2 = C2[row * N1 + col];
+    val = csub(val, csub(c1, c2));
+    if (second) {
+      if (I == J) {
+        cplx x = cadd(X[(int64_t)a * nv + b], cconj(X[(int64_t)b * nv + a]));
+        val = csub(val, cscale(x, 0.25));
+      }
+      if (a == b) {
+        cplx y = cadd(Y[I * nc + J], cconj(Y[J * nc + I]));
+        val = csub(val, cscale(y, 0.25));
+      }
+      cplx z = cadd(Z[row * N1 + col], cconj(Z[col * N1 + row]));
+      val = cadd(val, cscale(z, 0.5));
+    }
+    M11[idx] = val;
+  }
+}
+
+__global__ void unpack_kernel(const cplx* __restrict__ x2, int nc, int nw,
+                              int nv, cplx* __restrict__ Yt) {
+  const int64_t npair = (int64_t)nv * (nv - 1) / 2;
+  const int64_t total = (int64_t)nc * nv * nw * nv;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int b = idx % nv;
+    int64_t r = idx / nv;
+    int j = r % nw;
+    r /= nw;
+    int a = r % nv;
+    int I = r / nv;
+    int64_t base = ((int64_t)I * nw + j) * npair;
+    cplx val;
+    if (a < b)
+      val = x2[base + pair_index(a, b, nv)];
+    else if (a > b) {
+      val = x2[base + pair_index(b, a, nv)];
+      val.x = -val.x;
+      val.y = -val.y;
+    } else
+      val = cmake(0, 0);
+    Yt[idx] = val;
+  }
+}
+
+// one block per (I, j, a) row of the packed doubles
+__global__ void sigma2_kernel(const cplx* __restrict__ G,
+                              const cplx* __restrict__ x2,
+                              const double* __restrict__ eps, int nc, int nw,
+                              int nv, cplx* __restrict__ s2) {
+  const int64_t npair = (int64_t)nv * (nv - 1) / 2;
+  const int o = nc + nw;
+  const int64_t nrows = (int64_t)nc * nw * nv;
+  for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+    int a = row % nv;
+    int64_t r = row / nv;
+    int j = r % nw;
+    int I = r / nw;
+    int64_t base = ((int64_t)I * nw + j) * npair + pair_index(a, a + 1, nv) - (a + 1);
+    double e0 = eps[o + a] - eps[I] - eps[nc + j];
+    const cplx* Ga = G + (((int64_t)I * nv + a) * nw + j) * nv;
+    for (int b = a + 1 + threadIdx.x; b < nv; b += blockDim.x) {
+      cplx g1 = Ga[b];
+      cplx g2 = G[(((int64_t)I * nv + b) * nw + j) * nv + a];
+      int64_t d = base + b;
+      cplx x = x2[d];
+      double m22 = e0 + eps[o + b];
+      cplx out = csub(g2, g1);
+      out.x += m22 * x.x;
+      out.y += m22 * x.y;
+      s2[d] = out;
+    }
+  }
+}
+
+// F[I][j][a][b] = -(A[a][b] - A[b][a]) + T[a][b], A and T as [I][j][a][b]
+__global__ void pack_moment_kernel(const cplx* __restrict__ A,
+                                   const cplx* __restrict__ T, int nc, int nw,
+                                   int nv, cplx* __restrict__ out) {
+  const int64_t npair = (int64_t)nv * (nv - 1) / 2;
+  const int64_t nrows = (int64_t)nc * nw * nv;
+  for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+    int a = row % nv;
+    int64_t r = row / nv;
+    int j = r % nw;
+    int I = r / nw;
+    int64_t base = ((int64_t)I * nw + j) * npair + pair_index(a, a + 1, nv) - (a + 1);
+    int64_t blk = ((int64_t)I * nw + j) * nv * (int64_t)nv;
+    for (int b = a + 1 + threadIdx.x; b < nv; b += blockDim.x) {
+      cplx ab = A[blk + (int64_t)a * nv + b];
+      cplx ba = A[blk + (int64_t)b * nv + a];
+      cplx t = T[blk + (int64_t)a * nv + b];
+      out[base + b] = cadd(csub(ba, ab), t);
+    }
+  }
+}
+
+__global__ void diag_kernel(const cplx* M11, const double* eps, int nc,
+                            int nw, int nv, double* diag) {
+  const int64_t N1 = (int64_t)nc * nv;
+  const int64_t npair = (int64_t)nv * (nv - 1) / 2;
+  const int o = nc + nw;
+  const int64_t nrows = (int64_t)nc * nw * nv;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < N1;
+       s += (int64_t)gridDim.x * blockDim.x)
+    diag[s] = M11[s * N1 + s].x;
+  for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+    int a = row % nv;
+    int64_t r = row / nv;
+    int j = r % nw;
+    int I = r / nw;
+    int64_t base = N1 + ((int64_t)I * nw + j) * npair + pair_index(a, a + 1, nv) - (a + 1);
+    double e0 = eps[o + a] - eps[I] - eps[nc + j];
+    for (int b = a + 1 + threadIdx.x; b < nv; b += blockDim.x)
+      diag[base + b] = e0 + eps[o + b];
+  }
+}
+
+// ---------------------------------------------------- tall-skinny kernels
+constexpr int TSN = 16;  // n-tile of ts_dot
+
+__global__ void ts_dot_kernel(const cplx* __restrict__ A, int ma,
+                              const cplx* __restrict__ B, int mb, int64_t N,
+                              cplx* __restrict__ part) {
+  extern __shared__ cplx sh[];
+  cplx* sa = sh;             // [ma][TSN]
+  cplx* sb = sh + ma * TSN;  // [mb][TSN]
+  const int npairs = ma * mb;
+  const int per = (npairs + blockDim.x - 1) / blockDim.x;  // <= 16
+  double ar[16], ai[16];
+  for (int q = 0; q < 16; ++q) ar[q] = ai[q] = 0.0;
+  int64_t chunk = (N + gridDim.x - 1) / gridDim.x;
+  int64_t n0 = blockIdx.x * chunk, n1 = min(N, n0 + chunk);
+  for (int64_t t0 = n0; t0 < n1; t0 += TSN) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < (ma + mb) * TSN; e += blockDim.x) {
+      int vec = e / TSN, k = e % TSN;
+      int64_t n = t0 + k;
+      cplx val = cmake(0, 0);
+      if (n < n1) val = vec < ma ? A[(int64_t)vec * N + n] : B[(int64_t)(vec - ma) * N + n];
+      sh[e] = val;
+    }
+    __syncthreads();
+    for (int q = 0; q < per; ++q) {
+      int pr = threadIdx.x + q * blockDim.x;
+      if (pr >= npairs) break;
+      int i = pr / mb, j = pr % mb;
+      const cplx* x = sa + i * TSN;
+      const cplx* y = sb + j * TSN;
+      double sr = 0, si = 0;
+#pragma unroll
+      for (int k = 0; k < TSN; ++k) {
+        sr = fma(x[k].x, y[k].x, sr);
+        sr = fma(x[k].y, y[k].y, sr);
+        si = fma(x[k].x, y[k].y, si);
+        si = fma(-x[k].y, y[k].x, si);
+      }
+      ar[q] += sr;
+      ai[q] += si;
+    }
+  }
+  for (int q = 0; q < per; ++q) {
+    int pr = threadIdx.x + q * blockDim.x;
+    if (pr >= npairs) break;
+    part[(int64_t)pr * gridDim.x + blockIdx.x] = cmake(ar[q], ai[q]);
+  }
+}
+
+__global__ void ts_dot_reduce(const cplx* part, int npairs, int mb,
+                              int chunks, cplx* out, int ldo) {
+  int pr = blockIdx.x;
+  if (pr >= npairs) return;
+  double sr = 0, si = 0;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+    cplx v = part[(int64_t)pr * chunks + c];
+    sr += v.x;
+    si += v.y;
+  }
+  sr = block_sum(sr);
+  si = block_sum(si);
+  if (threadIdx.x == 0) out[(pr / mb) * ldo + (pr % mb)] = cmake(sr, si);
+}
+
+// out[r][n] = sum_i W[i][n] cw[i*ldc+r] + V[i][n] cv[i*ldc+r]
+__global__ void ts_combine_kernel(const cplx* __restrict__ V,
+                                  const cplx* __restrict__ cv,
+                                  const cplx* __restrict__ W,
+                                  const cplx* __restrict__ cw, int m, int ldc,
+                                  int k, int64_t N, cplx* __restrict__ out) {
+  extern __shared__ cplx coef[];  // [2][m][k]
+  for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
+    int i = e / k, r = e % k;
+    coef[e] = cv ? cv[i * ldc + r] : cmake(0, 0);
+    coef[m * k + e] = cw ? cw[i * ldc + r] : cmake(0, 0);
+  }
+  __syncthreads();
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    for (int r0 = 0; r0 < k; r0 += 8) {
+      double accr[8], acci[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) accr[q] = acci[q] = 0.0;
+      for (int i = 0; i < m; ++i) {
+        cplx vv = V ? V[(int64_t)i * N + n] : cmake(0, 0);
+        cplx ww = W ? W[(int64_t)i * N + n] : cmake(0, 0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          int r = r0 + q;
+          if (r < k) {
+            cplx a = coef[i * k + r];
+            cplx b = coef[m * k + i * k + r];
+            accr[q] += vv.x * a.x - vv.y * a.y + ww.x * b.x - ww.y * b.y;
+            acci[q] += vv.x * a.y + vv.y * a.x + ww.x * b.y + ww.y * b.x;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int r = r0 + q;
+        if (r < k) out[(int64_t)r * N + n] = cmake(accr[q], acci[q]);
+      }
+    }
+  }
+}
+
+// y[r] -= sum_i V[i] c[r*ldc + i]
+__global__ void ts_subtract_kernel(const cplx* __restrict__ V, int m,
+                                   const cplx* __restrict__ c, int ldc, int k,
+                                   int64_t N, cplx* __restrict__ y) {
+  extern __shared__ cplx coef[];  // [k][m]
+  for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
+    int r = e / m, i = e % m;
+    coef[e] = c[i * ldc + r];
+  }
+  __syncthreads();
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    for (int r0 = 0; r0 < k; r0 += 8) {
+      double accr[8], acci[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) accr[q] = acci[q] = 0.0;
+      for (int i = 0; i < m; ++i) {
+        cplx vv = V[(int64_t)i * N + n];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          int r = r0 + q;
+          if (r < k) {
+            cplx a = coef[r * m + i];
+            accr[q] += vv.x * a.x - vv.y * a.y;
+            acci[q] += vv.x * a.y + vv.y * a.x;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        int r = r0 + q;
+        if (r < k) {
+          cplx* d = y + (int64_t)r * N + n;
+          cplx o = *d;
+          *d = cmake(o.x - accr[q], o.y - acci[q]);
+        }
+      }
+    }
+  }
+}
+
+__global__ void resid_kernel(const cplx* __restrict__ AX,
+                             const cplx* __restrict__ X,
+                             const double* __restrict__ theta,
+                             const double* __restrict__ diag, int64_t N,
+                             cplx* __restrict__ t, double* part) {
+  const int r = blockIdx.y;
+  const double th = theta[r];
+  double acc = 0.0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    cplx ax = AX[(int64_t)r * N + n];
+    cplx x = X[(int64_t)r * N + n];
+    cplx res = cmake(ax.x - th * x.x, ax.y - th * x.y);
+    acc += res.x * res.x + res.y * res.y;
+    double den = th - diag[n];
+    if (fabs(den) < 1e-4) den = den < 0 ? -1e-4 : 1e-4;
+    t[(int64_t)r * N + n] = cscale(res, 1.0 / den);
+  }
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) part[r * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void reduce_rows_kernel(const double* part, int chunks,
+                                   double* out) {
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < chunks; c += blockDim.x)
+    acc += part[blockIdx.x * chunks + c];
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+__global__ void scale_vectors_kernel(cplx* x, const double* scale,
+                                     int64_t N) {
+  const int r = blockIdx.y;
+  const double sc = scale[r];
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x)
+    x[(int64_t)r * N + n] = cscale(x[(int64_t)r * N + n], sc);
+}
+
+
+__global__ void copy_view_kernel(int M, int N, double alpha, View src,
+                                 View dst) {
+  int64_t total = (int64_t)M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int r = idx / N, c = idx % N;
+    cplx v = src.p[vrow(src, r) + vcol(src, c)];
+    if (src.conj) v.y = -v.y;
+    dst.p[vrow(dst, r) + vcol(dst, c)] = cscale(v, alpha);
+  }
+}
+
+// one pass of an argmin over d[N] skipping the indices already chosen
+__global__ void argmin_kernel(const double* d, int64_t N, const int64_t* taken,
+                              int ntaken, double* pv, int64_t* pi) {
+  double best = 1e300;
+  int64_t bi = -1;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    double x = d[n];
+    if (x < best || (x == best && n < bi)) {
+      bool skip = false;
+      for (int q = 0; q < ntaken; ++q) skip |= (taken[q] == n);
+      if (!skip) {
+        best = x;
+        bi = n;
+      }
+    }
+  }
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      double v2 = sv[threadIdx.x + o];
+      int64_t i2 = si[threadIdx.x + o];
+      if (i2 >= 0 && (si[threadIdx.x] < 0 || v2 < sv[threadIdx.x] ||
+                      (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x]))) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = sv[0];
+    pi[blockIdx.x] = si[0];
+  }
+}
+
+__global__ void argmin_final(const double* pv, const int64_t* pi, int nb,
+                             int64_t* taken, int slot) {
+  if (threadIdx.x != 0) return;
+  double best = 1e300;
+  int64_t bi = -1;
+  for (int b = 0; b < nb; ++b)
+    if (pi[b] >= 0 && (bi < 0 || pv[b] < best || (pv[b] == best && pi[b] < bi))) {
+      best = pv[b];
+      bi = pi[b];
+    }
+  taken[slot] = bi;
+}
+
+// per vector: block partial argmax of |x|
+__global__ void absmax_kernel(const cplx* x, int64_t N, double* pv,
+                              int64_t* pi) {
+  const int r = blockIdx.y;
+  double best = -1.0;
+  int64_t bi = 0;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    cplx v = x[(int64_t)r * N + n];
+    double m = v.x * v.x + v.y * v.y;
+    if (m > best) {
+      best = m;
+      bi = n;
+    }
+  }
+  __shared__ double sv[256];
+  __shared__ int64_t si[256];
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      double v2 = sv[threadIdx.x + o];
+      int64_t i2 = si[threadIdx.x + o];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pv[r * gridDim.x + blockIdx.x] = sv[0];
+    pi[r * gridDim.x + blockIdx.x] = si[0];
+  }
+}
+
+__global__ void phase_apply_kernel(cplx* x, int64_t N, const double* pv,
+                                   const int64_t* pi, int nb) {
+  const int r = blockIdx.y;
+  __shared__ cplx ph;
+  if (threadIdx.x == 0) {
+    double best = -1.0;
+    int64_t bi = 0;
+    for (int b = 0; b < nb; ++b) {
+      double v = pv[r * nb + b];
+      int64_t i = pi[r * nb + b];
+      if (v > best || (v == best && i < bi)) {
+        best = v;
+        bi = i;
+      }
+    }
+    cplx v = x[(int64_t)r * N + bi];
+    double m = hypot(v.x, v.y);
+    ph = m > 0 ? cmake(v.x / m, -v.y / m) : cmake(1, 0);
+  }
+  __syncthreads();
+  cplx p = ph;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x)
+    x[(int64_t)r * N + n] = cmul(x[(int64_t)r * N + n], p);
+}
+
+
+// A[i][j] = (H[i][j] + conj(H[j][i])) / 2, H with leading dimension ldh
+__global__ void hermitize_kernel(const cplx* H, int ldh, int m, cplx* A) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       e < (int64_t)m * m; e += (int64_t)gridDim.x * blockDim.x) {
+    int i = e / m, j = e % m;
+    cplx a = H[(int64_t)i * ldh + j], b = H[(int64_t)j * ldh + i];
+    A[e] = cmake(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  }
+}
+
+// X[r][c] *= s[r]
+__global__ void scale_rows_kernel(cplx* X, int rows, int cols, int ld,
+                                  const double* sc) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       e < (int64_t)rows * cols; e += (int64_t)gridDim.x * blockDim.x) {
+    int r = e / cols, c = e % cols;
+    X[(int64_t)r * ld + c] = cscale(X[(int64_t)r * ld + c], sc[r]);
+  }
+}
+
+}  // namespace
+
+void scale_view(cudaStream_t s, int M, int N, double beta, View C, int batch) {
+  dim3 grid(grid1d((int64_t)M * N, 256), batch);
+  scale_view_kernel<<<grid, 256, 0, s>>>(M, N, beta, C);
+  CVS_CHECK_LAUNCH();
+}
+
+void hermiticity(cudaStream_t s, const cplx* B, int n, int64_t nmat,
+                 double* out_dev) {
+  CVS_CUDA(cudaMemsetAsync(out_dev, 0, 2 * sizeof(double), s));
+  herm_kernel<<<grid1d(nmat * n * (int64_t)n, 256), 256, 0, s>>>(B, n, nmat,
+                                                                out_dev);
+  CVS_CHECK_LAUNCH();
+}
+
+void t2_band(cudaStream_t s, const cplx* V, int a0, int na, int o, int v,
+             const double* eps, cplx* t2, cplx* g2, double* part, int nblk) {
+  t2_band_kernel<<<nblk, 256, 0, s>>>(V, a0, na, o, v, eps, t2, g2, part);
+  CVS_CHECK_LAUNCH();
+}
+
+void reduce_sum(cudaStream_t s, const double* in, int n, double* out) {
+  reduce_sum_kernel<<<1, 256, 0, s>>>(in, n, out);
+  CVS_CHECK_LAUNCH();
+}
+
+void m11_assemble(cudaStream_t s, int ncore, int nvirt, int o,
+                  const double* eps, const cplx* C1, const cplx* C2,
+                  const cplx* X, const cplx* Y, const cplx* Z, int second,
+                  cplx* M11) {
+  int64_t N1 = (int64_t)ncore * nvirt;
+  m11_kernel<<<grid1d(N1 * N1, 256), 256, 0, s>>>(ncore, nvirt, o, eps, C1,
+                                                   C2, X, Y, Z, second, M11);
+  CVS_CHECK_LAUNCH();
+}
+
+void unpack_doubles(cudaStream_t s, const cplx* x2, int ncore, int nval,
+                    int nvirt, cplx* Yt) {
+  int64_t total = (int64_t)ncore * nvirt * nval * nvirt;
+  unpack_kernel<<<grid1d(total, 256), 256, 0, s>>>(x2, ncore, nval, nvirt,
+                                                    Yt);
+  CVS_CHECK_LAUNCH();
+}
+
+void sigma2_finish(cudaStream_t s, const cplx* G, const cplx* x2,
+                   const double* eps, int ncore, int nval, int nvirt,
+                   cplx* s2) {
+  int64_t rows = (int64_t)ncore * nval * nvirt;
+  unsigned g = rows > 65535 * 8 ? 65535 * 8 : (unsigned)rows;
+  sigma2_kernel<<<g, 128, 0, s>>>(G, x2, eps, ncore, nval, nvirt, s2);
+  CVS_CHECK_LAUNCH();
+}
+
+void pack_moment_doubles(cudaStream_t s, const cplx* A, const cplx* T,
+                         int ncore, int nval, int nvirt, cplx* out) {
+  int64_t rows = (int64_t)ncore * nval * nvirt;
+  unsigned g = rows > 65535 * 8 ? 65535 * 8 : (unsigned)rows;
+  pack_moment_kernel<<<g, 128, 0, s>>>(A, T, ncore, nval, nvirt, out);
+  CVS_CHECK_LAUNCH();
+}
+
+void build_diag(cudaStream_t s, const cplx* M11, const double* eps,
+                int ncore, int nval, int nvirt, double* diag) {
+  int64_t rows = (int64_t)ncore * nval * nvirt;
+  unsigned g = rows > 65535 * 8 ? 65535 * 8 : (unsigned)rows;
+  diag_kernel<<<g, 128, 0, s>>>(M11, eps, ncore, nval, nvirt, diag);
+  CVS_CHECK_LAUNCH();
+}
+
+void ts_dot(cudaStream_t s, const cplx* A, int ma, const cplx* B, int mb,
+            int64_t N, cplx* part, cplx* out, int ldo) {
+  if (ma > 96) {
+    for (int i0 = 0; i0 < ma; i0 += 96)
+      ts_dot(s, A + (int64_t)i0 * N, std::min(96, ma - i0), B, mb, N, part,
+             out + (int64_t)i0 * ldo, ldo);
+    return;
+  }
+  if (ma * mb > 16 * 256 || ma + mb > 192) {
+    int g = std::max(1, std::min(192 - ma, 4096 / ma));
+    for (int j0 = 0; j0 < mb; j0 += g)
+      ts_dot(s, A, ma, B + (int64_t)j0 * N, std::min(g, mb - j0), N, part,
+             out + j0, ldo);
+    return;
+  }
+  int chunks = TS_CHUNKS;
+  size_t sh = (size_t)(ma + mb) * TSN * sizeof(cplx);
+  ts_dot_kernel<<<chunks, 256, sh, s>>>(A, ma, B, mb, N, part);
+  CVS_CHECK_LAUNCH();
+  ts_dot_reduce<<<ma * mb, 256, 0, s>>>(part, ma * mb, mb, chunks, out, ldo);
+  CVS_CHECK_LAUNCH();
+}
+
+void ts_combine(cudaStream_t s, const cplx* V, const cplx* cv, const cplx* W,
+                const cplx* cw, int m, int ldc, int k, int64_t N,
+                cplx* out) {
+  if (2 * (size_t)m * k * sizeof(cplx) > 96 * 1024) {
+    int g = std::max(1, (int)(96 * 1024 / (2 * (size_t)m * sizeof(cplx))));
+    CVS_REQUIRE(2 * (size_t)m * sizeof(cplx) <= 96 * 1024, -1, "ts_combine: m too large");
+    for (int r0 = 0; r0 < k; r0 += g)
+      ts_combine(s, V, cv ? cv + r0 : nullptr, W, cw ? cw + r0 : nullptr, m,
+                 ldc, std::min(g, k - r0), N, out + (int64_t)r0 * N);
+    return;
+  }
+  size_t sh = 2 * (size_t)m * k * sizeof(cplx);
+  ts_combine_kernel<<<grid1d(N, 256), 256, sh, s>>>(V, cv, W, cw, m, ldc, k,
+                                                    N, out);
+  CVS_CHECK_LAUNCH();
+}
+
+void ts_subtract(cudaStream_t s, const cplx* V, int m, const cplx* c, int ldc,
+                 int k, int64_t N, cplx* y) {
+  if ((size_t)m * k * sizeof(cplx) > 96 * 1024) {
+    int g = std::max(1, (int)(96 * 1024 / ((size_t)m * sizeof(cplx))));
+    for (int r0 = 0; r0 < k; r0 += g)
+      ts_subtract(s, V, m, c + r0, ldc, std::min(g, k - r0), N,
+                  y + (int64_t)r0 * N);
+    return;
+  }
+  size_t sh = (size_t)m * k * sizeof(cplx);
+  ts_subtract_kernel<<<grid1d(N, 256), 256, sh, s>>>(V, m, c, ldc, k, N, y);
+  CVS_CHECK_LAUNCH();
+}
+
+void residual_precond(cudaStream_t s, const cplx* AX, const cplx* X,
+                      const double* theta, const double* diag, int k,
+                      int64_t N, cplx* t, double* part, double* rnorm2) {
+  const int chunks = 304;
+  dim3 grid(chunks, k);
+  resid_kernel<<<grid, 256, 0, s>>>(AX, X, theta, diag, N, t, part);
+  CVS_CHECK_LAUNCH();
+  reduce_rows_kernel<<<k, 256, 0, s>>>(part, chunks, rnorm2);
+  CVS_CHECK_LAUNCH();
+}
+
+void scale_vectors(cudaStream_t s, cplx* x, const double* scale, int k,
+                   int64_t N) {
+  dim3 grid(grid1d(N, 256, 1216), k);
+  scale_vectors_kernel<<<grid, 256, 0, s>>>(x, scale, N);
+  CVS_CHECK_LAUNCH();
+}
+
+
+void copy_view(cudaStream_t s, int M, int N, double alpha, View src,
+               View dst) {
+  copy_view_kernel<<<grid1d((int64_t)M * N, 256), 256, 0, s>>>(M, N, alpha,
+                                                              src, dst);
+  CVS_CHECK_LAUNCH();
+}
+
+void k_smallest(cudaStream_t s, const double* d, int64_t N, int k,
+                int64_t* idx_dev, double* work) {
+  CVS_REQUIRE(k >= 1 && k <= 64 && k <= N, -1, "k_smallest: bad k");
+  const int nb = 304;
+  double* pv = work;
+  int64_t* pi = (int64_t*)(work + nb);
+  for (int q = 0; q < k; ++q) {
+    argmin_kernel<<<nb, 256, 0, s>>>(d, N, idx_dev, q, pv, pi);
+    CVS_CHECK_LAUNCH();
+    argmin_final<<<1, 32, 0, s>>>(pv, pi, nb, idx_dev, q);
+    CVS_CHECK_LAUNCH();
+  }
+}
+
+void phase_fix(cudaStream_t s, cplx* x, int k, int64_t N, double* work) {
+  const int nb = 152;
+  double* pv = work;
+  int64_t* pi = (int64_t*)(work + (size_t)nb * k);
+  dim3 grid(nb, k);
+  absmax_kernel<<<grid, 256, 0, s>>>(x, N, pv, pi);
+  CVS_CHECK_LAUNCH();
+  phase_apply_kernel<<<grid, 256, 0, s>>>(x, N, pv, pi, nb);
+  CVS_CHECK_LAUNCH();
+}
+
+void init_kernel_attributes() {
+  CVS_CUDA(cudaFuncSetAttribute(ts_combine_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024));
+  CVS_CUDA(cudaFuncSetAttribute(ts_subtract_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024));
+  CVS_CUDA(cudaFuncSetAttribute(ts_dot_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024));
+}
+
+
+void hermitize(cudaStream_t s, const cplx* H, int ldh, int m, cplx* A) {
+  hermitize_kernel<<<grid1d((int64_t)m * m, 256), 256, 0, s>>>(H, ldh, m, A);
+  CVS_CHECK_LAUNCH();
+}
+
+void scale_rows(cudaStream_t s, cplx* X, int rows, int cols, int ld,
+                const double* sc) {
+  scale_rows_kernel<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(
+      X, rows, cols, ld, sc);
+  CVS_CHECK_LAUNCH();
+}
+
+}  // namespace cvs

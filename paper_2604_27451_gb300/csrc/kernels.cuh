@@ -1,0 +1,109 @@
+// Host-side launchers of the libcvsadc device kernels.
+#pragma once
+
+#include "common.cuh"
+
+namespace cvs {
+
+// ------------------------------------------------------------- GEMMs
+// C = alpha * A * B + beta * C, complex, two-mode views, batch over z.
+void zgemm_f64(cudaStream_t s, int M, int N, int K, double alpha, View A,
+               View B, double beta, View C, int batch = 1);
+
+// Same contract on the tcgen05 tensor cores: A and B are split into
+// bf16 hi/lo parts, three products per real product, FP32 accumulation.
+// `work` must hold tc_workspace_bytes(M, N, K) bytes.
+size_t tc_workspace_bytes(int M, int N, int K);
+void zgemm_tc(cudaStream_t s, int M, int N, int K, double alpha, View A,
+              View B, double beta, View C, void* work, size_t work_bytes);
+bool tc_available();
+
+// C = beta * C over a view
+void scale_view(cudaStream_t s, int M, int N, double beta, View C, int batch);
+
+// --------------------------------------------------------- utilities
+// max |B_pq - conj(B_qp)| and max |B_pq| over nmat n x n matrices;
+// out[0], out[1] (device doubles, zeroed by the launcher).
+void hermiticity(cudaStream_t s, const cplx* B, int n, int64_t nmat,
+                 double* out_dev);
+
+// ------------------------------------------------------------ MP2 / t2
+// From V[(al, i), (b, j)] = (a i | b j) for a = a0 + al, write
+// g2[i][j][a][b] = <ab||ij> = V[(al,i),(b,j)] - V[(al,j),(b,i)] and
+// t2 = g2 / (e_i + e_j - e_a - e_b) for a in [a0, a0+na); accumulate
+// 1/4 |g2|^2 / den into per-block partials part[nblk].
+void t2_band(cudaStream_t s, const cplx* V, int a0, int na, int o, int v,
+             const double* eps, cplx* t2, cplx* g2, double* part, int nblk);
+// Deterministic sum of n doubles into *out (device).
+void reduce_sum(cudaStream_t s, const double* in, int n, double* out);
+
+// ----------------------------------------------------------------- M11
+// M11 assembly from the pieces (see solver.cu).
+void m11_assemble(cudaStream_t s, int ncore, int nvirt, int o,
+                  const double* eps, const cplx* C1, const cplx* C2,
+                  const cplx* X, const cplx* Y, const cplx* Z, int second,
+                  cplx* M11);
+
+// --------------------------------------------------------------- sigma
+// Yt[I][a][j][b] = antisymmetric unpack of packed doubles x2.
+void unpack_doubles(cudaStream_t s, const cplx* x2, int ncore, int nval,
+                    int nvirt, cplx* Yt);
+// sigma2[d] = -(G[I,a,j,b] - G[I,b,j,a]) + (e_a+e_b-e_I-e_j) x2[d]
+void sigma2_finish(cudaStream_t s, const cplx* G, const cplx* x2,
+                   const double* eps, int ncore, int nval, int nvirt,
+                   cplx* s2);
+// pack an antisymmetric-by-construction full tensor F[I][j][a][b] with
+// F = -(A[a][b] - A[b][a]) + T[a][b] into packed doubles (a < b).
+void pack_moment_doubles(cudaStream_t s, const cplx* A, const cplx* T,
+                         int ncore, int nval, int nvirt, cplx* out);
+// diagonal of M: dM11 (from M11) and M22 on the fly, into diag[N] (real)
+void build_diag(cudaStream_t s, const cplx* M11, const double* eps,
+                int ncore, int nval, int nvirt, double* diag);
+
+// ------------------------------------------------------------ Davidson
+// out[i*ldo + j] = sum_n conj(A[i][n]) B[j][n], i < ma, j < mb
+// part must hold ma*mb*TS_CHUNKS complex.
+constexpr int TS_CHUNKS = 304;
+void ts_dot(cudaStream_t s, const cplx* A, int ma, const cplx* B, int mb,
+            int64_t N, cplx* part, cplx* out, int ldo);
+// out[r][n] = sum_i W[i][n] cw[i*ldc + r] + V[i][n] cv[i*ldc + r], r < k
+// (either input may be NULL); out may not alias inputs.
+void ts_combine(cudaStream_t s, const cplx* V, const cplx* cv,
+                const cplx* W, const cplx* cw, int m, int ldc, int k,
+                int64_t N, cplx* out);
+// t[r] = (AX[r] - theta[r] X[r]) / (theta[r] - diag), |denominator|
+// clamped to >= 1e-4; rnorm2[r] = ||AX[r] - theta[r] X[r]||^2.
+void residual_precond(cudaStream_t s, const cplx* AX, const cplx* X,
+                      const double* theta, const double* diag, int k,
+                      int64_t N, cplx* t, double* part, double* rnorm2);
+// y[r] -= sum_i V[i] c[i*ldc+r] for r < k (classical Gram-Schmidt step;
+// c laid out as ts_dot writes it)
+void ts_subtract(cudaStream_t s, const cplx* V, int m, const cplx* c,
+                 int ldc, int k, int64_t N, cplx* y);
+// x[r] *= scale[r]
+void scale_vectors(cudaStream_t s, cplx* x, const double* scale, int k,
+                   int64_t N);
+// generic strided copy dst(r, c) = alpha * src(r, c)
+void copy_view(cudaStream_t s, int M, int N, double alpha, View src, View dst);
+// indices of the k smallest entries of d[N] (ascending), k <= 64
+void k_smallest(cudaStream_t s, const double* d, int64_t N, int k,
+                int64_t* idx_dev, double* work);
+// make the largest-modulus entry of each of k vectors real positive
+void phase_fix(cudaStream_t s, cplx* x, int k, int64_t N, double* work);
+// A = (H + H^H)/2 for an m x m block of H (leading dimension ldh)
+void hermitize(cudaStream_t s, const cplx* H, int ldh, int m, cplx* A);
+// X[r][c] *= sc[r] (device scale vector)
+void scale_rows(cudaStream_t s, cplx* X, int rows, int cols, int ld,
+                const double* sc);
+// one-time kernel attribute setup for the current device
+void init_kernel_attributes();
+
+// ---------------------------------------------------- Jacobi (FP64)
+// Hermitian eigensolver: A [n][n] row-major (destroyed), eigenvalues w
+// ascending, eigenvectors as columns of Vec [n][n].  One CTA, cyclic
+// round-robin (Brent-Luk) ordering; at most max_sweeps sweeps.
+// info_dev[0] = sweeps used (as double), [1] = final off-norm ratio.
+void jacobi_eigh(cudaStream_t s, cplx* A, int n, double* w, cplx* Vec,
+                 int max_sweeps, double* info_dev);
+
+}  // namespace cvs

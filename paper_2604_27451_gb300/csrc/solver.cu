@@ -1,0 +1,1076 @@
+// libcvsadc host orchestration and C ABI.
+//
+// Stages (section "Implementation and Computational Details"):
+//   ingest      copy inputs to the device, check B^P and dipoles Hermitian
+//   fns         (tau > 0) MP2 vv density (Eq. 15), natural spinors (Eq. 17),
+//               truncation, semicanonicalisation (Eqs. 18-20), rotation of B^P
+//   mp2         t2 and E_MP2 from (ai|bj) = sum_P B^P_ai B^P_bj
+//   m11         core-singles block through second order
+//   moments     modified transition moments through first order
+//   davidson    block Davidson on sigma = M x, FP64 subspace algebra
+//   refine      (mixed precision) FP64 sigma on the converged vectors
+//
+// The element formulas (negative-denominator t2, CVS basis operators
+// a_a^+ a_I and a_a^+ a_b^+ a_I a_j):
+//   M11_{Ia,Jb} = d_IJ d_ab (e_a - e_I) - <aJ||bI> - 1/4 d_IJ Ivv_ab
+//                 - 1/4 d_ab Joo_IJ + 1/2 K_{Ia,Jb}
+//   M21_{(Ijab),(Kc)} = -d_IK <ab||cj> + d_ac <Kb||Ij> - d_bc <Ka||Ij>
+//   M22 = diag(e_a + e_b - e_I - e_j)
+// Through B^P the couplings read
+//   sigma2_{Ijab} = -(G_{Ia,jb} - G_{Ib,ja}) + M22 x2,
+//   G_{Ia,jb} = sum_P (Y - W)^P_{aI} B^P_{bj} - B^P_{aI} V^P_{bj},
+//   Y^P_{aI} = sum_c B^P_ac x_Ic, W^P_{aI} = sum_K B^P_KI x_Ka,
+//   V^P_{bj} = sum_K B^P_Kj x_Kb,
+//   sigma1_{Kc} = M11 x1 - sum_{P,a} B^P_ca S^P_{aK} + sum_{P,I} B^P_IK S^P_{cI}
+//                 - sum_{P,j} B^P_jK R^P_{cj},
+//   S^P_{aI} = sum_{jb} y_{Ijab} B^P_jb, R^P_{cj} = sum_{Ib} y_{Ijcb} B^P_Ib,
+// with y the antisymmetric unpacking of x2; <pq||rs> is never formed.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/cvsadc.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+using namespace cvs;
+
+namespace {
+
+// ------------------------------------------------------- allocation registry
+// Every live device buffer, so that a view built on a pointer into one can
+// be bounds-checked on the host before any kernel reads through it.
+std::mutex g_reg_mu;
+std::map<uintptr_t, size_t> g_reg;
+
+void reg_add(const void* p, size_t b) {
+  std::lock_guard<std::mutex> l(g_reg_mu);
+  g_reg[(uintptr_t)p] = b;
+}
+void reg_del(const void* p) {
+  std::lock_guard<std::mutex> l(g_reg_mu);
+  g_reg.erase((uintptr_t)p);
+}
+// complex elements from p to the end of its registered buffer, or -1
+int64_t ext_from(const void* p) {
+  std::lock_guard<std::mutex> l(g_reg_mu);
+  uintptr_t a = (uintptr_t)p;
+  auto it = g_reg.upper_bound(a);
+  if (it == g_reg.begin()) return -1;
+  --it;
+  if (a >= it->first + it->second) return -1;
+  return (int64_t)((it->first + it->second - a) / sizeof(cplx));
+}
+struct RegGuard {  // registers a caller buffer for the duration of a call
+  const void* p;
+  RegGuard(const void* p_, size_t b) : p(p_) { reg_add(p, b); }
+  ~RegGuard() { reg_del(p); }
+};
+
+View checked(View v) {
+  if (v.ext < 0) v.ext = ext_from(v.p);
+  return v;
+}
+
+// ------------------------------------------------------------ device buffer
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) {
+      reg_del(p);
+      cudaFree(p);
+    }
+    p = nullptr;
+    bytes = 0;
+  }
+  void ensure(size_t b) {
+    if (b <= bytes && p) return;
+    release();
+    if (b == 0) return;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      p = nullptr;
+      char msg[160];
+      snprintf(msg, sizeof msg, "cudaMalloc of %.3f GB failed", b / 1e9);
+      throw Error{CVSADC_ENOMEM, msg};
+    }
+    bytes = b;
+    reg_add(p, b);
+  }
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+  cplx* c() const { return (cplx*)p; }
+  double* d() const { return (double*)p; }
+};
+
+bool verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("CVSADC_VERBOSE");
+    v = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+}  // namespace
+
+struct cvsadc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+
+  // prepared problem
+  bool prepared = false;
+  int ncore = 0, nval = 0, nvirt = 0, nvirt_in = 0, naux = 0, o = 0, n = 0;
+  int64_t N1 = 0, npair = 0, N2 = 0, N = 0;
+  bool has_dip = false, has_fns = false;
+  double emp2 = 0.0;
+  DBuf eps, B, dip, t2, g2, M11, diag, F, fns_occ, fns_U;
+
+  // scratch
+  DBuf s_big1, s_big2, s_S, s_R, s_Y, s_V, s_part, s_small, s_tc;
+  DBuf dv_V, dv_W, dv_X, dv_AX, dv_T, dv_H, dv_A, dv_U, dv_w, dv_misc;
+
+  void sync() { CVS_CUDA(cudaStreamSynchronize(stream)); }
+};
+
+namespace {
+
+// --------------------------------------------------------------- GEMM hub
+void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
+          View B, double beta, View C, int batch = 1) {
+  A = checked(A);
+  B = checked(B);
+  C = checked(C);
+  check_view(A, M, K, batch, "A");
+  check_view(B, K, N, batch, "B");
+  check_view(C, M, N, batch, "C");
+  if (prec == CVSADC_MIXED_BF16X3 && batch == 1 && tc_available()) {
+    size_t need = tc_workspace_bytes(M, N, K);
+    c->s_tc.ensure(need);
+    zgemm_tc(c->stream, M, N, K, alpha, A, B, beta, C, c->s_tc.p, need);
+    return;
+  }
+  if (prec == CVSADC_MIXED_BF16X3 && batch > 1 && tc_available()) {
+    size_t need = tc_workspace_bytes(M, N, K);
+    c->s_tc.ensure(need);
+    for (int z = 0; z < batch; ++z) {
+      View a = A, b = B, cc = C;
+      a.p += z * A.batch;
+      b.p += z * B.batch;
+      cc.p += z * C.batch;
+      if (a.ext >= 0) a.ext -= z * A.batch;
+      if (b.ext >= 0) b.ext -= z * B.batch;
+      if (cc.ext >= 0) cc.ext -= z * C.batch;
+      zgemm_tc(c->stream, M, N, K, alpha, a, b, beta, cc, c->s_tc.p, need);
+    }
+    return;
+  }
+  zgemm_f64(c->stream, M, N, K, alpha, A, B, beta, C, batch);
+}
+
+void gemm64(cvsadc_ctx* c, int M, int N, int K, double alpha, View A,
+            View B, double beta, View C, int batch = 1) {
+  A = checked(A);
+  B = checked(B);
+  C = checked(C);
+  check_view(A, M, K, batch, "A");
+  check_view(B, K, N, batch, "B");
+  check_view(C, M, N, batch, "C");
+  zgemm_f64(c->stream, M, N, K, alpha, A, B, beta, C, batch);
+}
+
+void copyv(cvsadc_ctx* c, int M, int N, double alpha, View src, View dst) {
+  src = checked(src);
+  dst = checked(dst);
+  check_view(src, M, N, 1, "copy src");
+  check_view(dst, M, N, 1, "copy dst");
+  copy_view(c->stream, M, N, alpha, src, dst);
+}
+
+void upload(cvsadc_ctx* c, DBuf& dst, const void* src, size_t bytes,
+            bool device_ptrs) {
+  dst.ensure(bytes);
+  CVS_CUDA(cudaMemcpyAsync(dst.p, src, bytes,
+                           device_ptrs ? cudaMemcpyDeviceToDevice
+                                       : cudaMemcpyHostToDevice,
+                           c->stream));
+}
+
+void download(cvsadc_ctx* c, void* dst, const void* src, size_t bytes,
+              bool device_ptrs) {
+  CVS_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                           device_ptrs ? cudaMemcpyDeviceToDevice
+                                       : cudaMemcpyDeviceToHost,
+                           c->stream));
+}
+
+void check_hermitian(cvsadc_ctx* c, const cplx* M, int n, int64_t nmat,
+                     const char* what) {
+  c->s_small.ensure(4096);
+  hermiticity(c->stream, M, n, nmat, c->s_small.d());
+  double h[2];
+  CVS_CUDA(cudaMemcpyAsync(h, c->s_small.p, sizeof h, cudaMemcpyDeviceToHost,
+                           c->stream));
+  c->sync();
+  if (h[0] > 1e-12 * std::max(h[1], 1e-300)) {
+    char msg[200];
+    snprintf(msg, sizeof msg, "%s is not Hermitian: max|M-M^H| = %.3e, max|M| = %.3e",
+             what, h[0], h[1]);
+    throw Error{CVSADC_ENONHERM, msg};
+  }
+}
+
+// ------------------------------------------------------------------ t2
+// t2[i][j][a][b], g2 = <ab||ij>, E_MP2; B is [L][n][n] with o occupied.
+void build_t2(cvsadc_ctx* c, int prec, const cplx* B, const double* eps,
+              int o, int v, int L, DBuf& t2, DBuf& g2, double* emp2) {
+  const int n = o + v;
+  const int64_t nn = (int64_t)n * n;
+  const int64_t vo = (int64_t)v * o;
+  const size_t tsz = (size_t)o * o * v * v * sizeof(cplx);
+  t2.ensure(tsz);
+  g2.ensure(tsz);
+  // band over a so that the (ai|bj) band stays within ~4 GB
+  int64_t per_a = (int64_t)o * vo * sizeof(cplx);
+  int na = (int)std::max<int64_t>(1, std::min<int64_t>(v, (4LL << 30) / per_a));
+  c->s_big1.ensure((size_t)na * per_a);
+  const int nblk = 608;
+  c->s_part.ensure(nblk * sizeof(double) + 64);
+  CVS_CUDA(cudaMemsetAsync(c->s_part.p, 0, nblk * sizeof(double), c->stream));
+  for (int a0 = 0; a0 < v; a0 += na) {
+    int nb = std::min(na, v - a0);
+    // V[(al,i),(b,j)] = sum_P B^P_{o+a0+al, i} B^P_{o+b, j}
+    View A = rows2(view(B + (int64_t)(o + a0) * n, 0, nn), n, 1, o);
+    View Bv = cols2(view(B + (int64_t)o * n, nn, 0), n, 1, o);
+    View C = view(c->s_big1.p, vo, 1);
+    gemm(c, prec, nb * o, (int)vo, L, 1.0, A, Bv, 0.0, C);
+    t2_band(c->stream, c->s_big1.c(), a0, nb, o, v, eps, t2.c(), g2.c(),
+            c->s_part.d(), nblk);
+  }
+  double* dE = (double*)((char*)c->s_part.p + nblk * sizeof(double));
+  reduce_sum(c->stream, c->s_part.d(), nblk, dE);
+  CVS_CUDA(cudaMemcpyAsync(emp2, dE, sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream));
+  c->sync();
+}
+
+// ------------------------------------------------------------------ M11
+void build_m11(cvsadc_ctx* c, int prec) {
+  const int nc = c->ncore, v = c->nvirt, o = c->o, n = c->n, L = c->naux;
+  const int64_t nn = (int64_t)n * n, N1 = c->N1;
+  const cplx* B = c->B.c();
+  const cplx* t2 = c->t2.c();
+  const cplx* g2 = c->g2.c();
+  c->M11.ensure(N1 * N1 * sizeof(cplx));
+  size_t need = ((size_t)v * v * nc * nc + 2 * N1 * N1 + (size_t)v * v + nc * nc) *
+                sizeof(cplx);
+  c->s_big2.ensure(need);
+  cplx* C1 = c->s_big2.c();
+  cplx* C2 = C1 + (size_t)v * v * nc * nc;
+  cplx* Z = C2 + N1 * N1;
+  cplx* X = Z + N1 * N1;
+  cplx* Y = X + (size_t)v * v;
+  // C1[(a,b),(J,I)] = (ab|JI)
+  gemm(c, prec, v * v, nc * nc, L, 1.0,
+       rows2(view(B + (int64_t)o * n + o, 0, nn), n, 1, v),
+       cols2(view(B, nn, 0), n, 1, nc), 0.0, view(C1, nc * nc, 1));
+  // C2[(I,a),(J,b)] = (aI|Jb)
+  gemm(c, prec, (int)N1, (int)N1, L, 1.0,
+       rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v),
+       cols2(view(B + o, nn, 0), n, 1, v), 0.0, view(C2, N1, 1));
+  const int64_t vv = (int64_t)v * v, ovv = (int64_t)o * vv;
+  // X_ab = sum_{kl,c} t^{ac}_{kl} conj(<bc||kl>)
+  gemm(c, prec, v, v, o * o * v, 1.0, cols2(view(t2, v, 0), vv, 1, v),
+       conj_of(rows2(view(g2, 0, v), vv, 1, v)), 0.0, view(X, v, 1));
+  // Y_IJ = sum_{k,cd} t^{cd}_{Ik} conj(<cd||Jk>)
+  gemm(c, prec, nc, nc, (int)ovv, 1.0, view(t2, ovv, 1),
+       conj_of(view(g2, 1, ovv)), 0.0, view(Y, nc, 1));
+  // Z_{Ia,Jb} = sum_{kc} t^{ac}_{Ik} conj(<bc||Jk>)
+  gemm(c, prec, (int)N1, (int)N1, o * v, 1.0,
+       cols2(rows2(view(t2, 0, 0), ovv, v, v), vv, 1, v),
+       conj_of(cols2(rows2(view(g2, 0, 0), vv, 1, v), ovv, v, v)), 0.0,
+       view(Z, N1, 1));
+  m11_assemble(c->stream, nc, v, o, c->eps.d(), C1, C2, X, Y, Z, 1,
+               c->M11.c());
+}
+
+// ------------------------------------------------------ transition moments
+void build_moments(cvsadc_ctx* c, int prec) {
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n;
+  const int64_t N1 = c->N1, N = c->N, vv = (int64_t)v * v,
+                ovv = (int64_t)o * vv;
+  const cplx* t2 = c->t2.c();
+  c->F.ensure(3 * N * sizeof(cplx));
+  size_t blk = (size_t)nc * nw * vv;
+  c->s_big2.ensure(2 * blk * sizeof(cplx));
+  cplx* tmp = c->s_big2.c();
+  cplx* T2 = tmp + blk;
+  for (int x = 0; x < 3; ++x) {
+    const cplx* d = c->dip.c() + (int64_t)x * n * n;
+    cplx* Fs = c->F.c() + (int64_t)x * N;
+    cplx* Fd = Fs + N1;
+    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 0\n", x); }
+    // F_S[I][a] = d_{aI} + sum_{kc} t^{ac}_{Ik} d_{kc}
+    copyv(c, nc, v, 1.0, view(d + (int64_t)o * n, 1, n),
+              view(Fs, v, 1));
+    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 1\n", x); }
+    gemm(c, prec, (int)N1, 1, o * v, 1.0,
+         cols2(rows2(view(t2, 0, 0), ovv, v, v), vv, 1, v),
+         rows2(view(d + o, 0, 0), n, 1, v), 1.0, view(Fs, 1, 1));
+    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 2\n", x); }
+    // tmp[I][j][a][b] = sum_c d_ac t^{cb}_{Ij}   (batched over I)
+    gemm(c, prec, v, nw * v, v, 1.0, view(d + (int64_t)o * n + o, n, 1),
+         batched(cols2(view(t2 + (int64_t)nc * vv, v, 0), vv, 1, v), ovv),
+         0.0, batched(cols2(view(tmp, v, 0), vv, 1, v), (int64_t)nw * vv), nc);
+    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 3\n", x); }
+    // T2[I][j][ab] = sum_k d_kI t^{ab}_{kj} - sum_k d_kj t^{ab}_{kI}
+    gemm(c, prec, nc, nw * (int)vv, o, 1.0, view(d, 1, n),
+         view(t2 + (int64_t)nc * vv, ovv, 1), 0.0, view(T2, nw * vv, 1));
+    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 4\n", x); }
+    gemm(c, prec, nw, nc * (int)vv, o, -1.0, view(d + nc, 1, n),
+         view(t2, ovv, 1), 1.0, cols2(view(T2, vv, 0), nw * vv, 1, (int)vv));
+    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 5\n", x); }
+    pack_moment_doubles(c->stream, tmp, T2, nc, nw, v, Fd);
+  }
+}
+
+// ----------------------------------------------------------------- sigma
+void sigma_impl(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int nvec) {
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
+            L = c->naux;
+  const int64_t nn = (int64_t)n * n, N1 = c->N1, N = c->N;
+  const int64_t wv = (int64_t)nw * v, vL = (int64_t)v * L;
+  const cplx* B = c->B.c();
+  size_t big = (size_t)N1 * wv * sizeof(cplx);
+  c->s_big1.ensure(big);
+  c->s_big2.ensure(big);
+  c->s_S.ensure((size_t)N1 * L * sizeof(cplx));
+  c->s_R.ensure((size_t)wv * L * sizeof(cplx));
+  c->s_Y.ensure((size_t)N1 * L * sizeof(cplx));
+  c->s_V.ensure((size_t)wv * L * sizeof(cplx));
+  cplx* Yt = c->s_big1.c();
+  cplx* G = c->s_big2.c();
+  cplx* S = c->s_S.c();
+  cplx* R = c->s_R.c();
+  cplx* Y = c->s_Y.c();
+  cplx* Vv = c->s_V.c();
+  for (int q = 0; q < nvec; ++q) {
+    const cplx* x1 = x + q * N;
+    const cplx* x2 = x1 + N1;
+    cplx* s1 = sig + q * N;
+    cplx* s2 = s1 + N1;
+    unpack_doubles(c->stream, x2, nc, nw, v, Yt);
+    // S[(I,a)][P] = sum_{jb} y_{Ijab} B^P_{jb}
+    gemm(c, prec, (int)N1, L, (int)wv, 1.0, view(Yt, wv, 1),
+         rows2(view(B + (int64_t)nc * n + o, 0, nn), n, 1, v), 0.0,
+         view(S, L, 1));
+    // R[(c,j)][P] = sum_{Ib} y_{Ijcb} B^P_{Ib}
+    gemm(c, prec, (int)wv, L, (int)N1, 1.0,
+         cols2(view(Yt, v, 0), wv * v, 1, v),
+         rows2(view(B + o, 0, nn), n, 1, v), 0.0, view(R, L, 1));
+    // sigma1 (M12 x2)
+    gemm(c, prec, nc, v, (int)vL, -1.0, view(S, vL, 1),
+         rows2(view(B + (int64_t)o * n + o, 0, n), 1, nn, L), 0.0,
+         view(s1, v, 1));
+    gemm(c, prec, nc, v, nc * L, 1.0, cols2(view(B, 1, 0), n, nn, L),
+         rows2(view(S, 0, L), vL, 1, L), 1.0, view(s1, v, 1));
+    gemm(c, prec, nc, v, nw * L, -1.0,
+         cols2(view(B + (int64_t)nc * n, 1, 0), n, nn, L),
+         view(R, 1, (int64_t)nw * L), 1.0, view(s1, v, 1));
+    // Y[(I,a)][P] = sum_c x_Ic B^P_ac - sum_K x_Ka B^P_KI
+    gemm(c, prec, nc, (int)vL, v, 1.0, view(x1, v, 1),
+         cols2(view(B + (int64_t)o * n + o, 1, 0), n, nn, L), 0.0,
+         view(Y, vL, 1));
+    gemm(c, prec, v, nc * L, nc, -1.0, view(x1, 1, v),
+         cols2(view(B, n, 0), 1, nn, L), 1.0,
+         cols2(view(Y, L, 0), vL, 1, L));
+    // Vv[(j,b)][P] = sum_K x_Kb B^P_{K j}
+    gemm(c, prec, v, nw * L, nc, 1.0, view(x1, 1, v),
+         cols2(view(B + nc, n, 0), 1, nn, L), 0.0,
+         cols2(view(Vv, L, 0), vL, 1, L));
+    // G[(I,a)][(j,b)] = sum_P Y B^P_{bj} - sum_P B^P_{aI} Vv
+    gemm(c, prec, (int)N1, (int)wv, L, 1.0, view(Y, L, 1),
+         cols2(view(B + (int64_t)o * n + nc, nn, 0), 1, n, v), 0.0,
+         view(G, wv, 1));
+    gemm(c, prec, (int)N1, (int)wv, L, -1.0,
+         rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v), view(Vv, 1, L),
+         1.0, view(G, wv, 1));
+    sigma2_finish(c->stream, G, x2, c->eps.d(), nc, nw, v, s2);
+    // sigma1 += M11 x1 (dense product, FP64 path for the small block)
+    gemm64(c, (int)N1, 1, (int)N1, 1.0, view(c->M11.c(), N1, 1),
+              view(x1, 1, 0), 1.0, view(s1, 1, 0));
+  }
+}
+
+// --------------------------------------------------------------- FNS
+void build_fns(cvsadc_ctx* c, int prec, double tau) {
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt_in, o = c->o,
+            L = c->naux;
+  const int n = o + v;
+  (void)nc;
+  (void)nw;
+  // canonical t2 (and <ab||ij>) for the density
+  DBuf t2, g2;
+  double e_can = 0.0;
+  build_t2(c, prec, c->B.c(), c->eps.d(), o, v, L, t2, g2, &e_can);
+  // D_ab = 1/2 sum_{cij} t^{ac}_{ij} conj(t^{bc}_{ij})
+  DBuf D;
+  D.ensure((size_t)v * v * sizeof(cplx));
+  const int64_t vv = (int64_t)v * v;
+  gemm(c, prec, v, v, o * o * v, 0.5, cols2(view(t2.p, v, 0), vv, 1, v),
+       conj_of(rows2(view(t2.p, 0, v), vv, 1, v)), 0.0, view(D.p, v, 1));
+  t2.release();
+  g2.release();
+  // Hermitian part for the eigensolver
+  DBuf A, Vec, w;
+  A.ensure(vv * sizeof(cplx));
+  Vec.ensure(vv * sizeof(cplx));
+  w.ensure(v * sizeof(double) + 64);
+  hermitize(c->stream, D.c(), v, v, A.c());
+  c->s_small.ensure(4096);
+  jacobi_eigh(c->stream, A.c(), v, w.d(), Vec.c(), 40, c->s_small.d());
+  std::vector<double> occ_asc(v);
+  CVS_CUDA(cudaMemcpyAsync(occ_asc.data(), w.p, v * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->stream));
+  c->sync();
+  // descending occupations; keep n >= tau (degenerate pairs kept together)
+  std::vector<int> keep;
+  for (int k = v - 1; k >= 0; --k)
+    if (occ_asc[k] >= tau * (1.0 - 1e-10)) keep.push_back(k);
+  int vk = (int)keep.size();
+  CVS_REQUIRE(vk >= 2, CVSADC_EINVAL, "FNS threshold keeps fewer than 2 virtuals");
+  std::vector<double> occ_desc(v);
+  for (int k = 0; k < v; ++k) occ_desc[k] = occ_asc[v - 1 - k];
+  c->fns_occ.ensure(v * sizeof(double));
+  CVS_CUDA(cudaMemcpyAsync(c->fns_occ.p, occ_desc.data(), v * sizeof(double),
+                           cudaMemcpyHostToDevice, c->stream));
+  // V~ columns (descending occupation order) gathered into Vt [v][vk]
+  DBuf Vt;
+  Vt.ensure((size_t)v * vk * sizeof(cplx));
+  for (int q = 0; q < vk; ++q)
+    copyv(c, v, 1, 1.0, view(Vec.c() + keep[q], v, 1),
+              view(Vt.c() + q, vk, 1));
+  // F^NS = V~^H diag(eps_v) V~ (Eq. 18): scale rows of V~ by eps_v, GEMM
+  DBuf EV, Fns, Fh, Z, et;
+  EV.ensure((size_t)v * vk * sizeof(cplx));
+  Fns.ensure((size_t)vk * vk * sizeof(cplx));
+  CVS_CUDA(cudaMemcpyAsync(EV.p, Vt.p, (size_t)v * vk * sizeof(cplx),
+                           cudaMemcpyDeviceToDevice, c->stream));
+  scale_rows(c->stream, EV.c(), v, vk, vk, c->eps.d() + o);
+  gemm64(c, vk, vk, v, 1.0, conj_of(trans(view(Vt.p, vk, 1))),
+            view(EV.p, vk, 1), 0.0, view(Fns.p, vk, 1));
+  // Hermitise and diagonalise (Eq. 19)
+  Fh.ensure((size_t)vk * vk * sizeof(cplx));
+  Z.ensure((size_t)vk * vk * sizeof(cplx));
+  et.ensure(vk * sizeof(double) + 64);
+  hermitize(c->stream, Fns.c(), vk, vk, Fh.c());
+  jacobi_eigh(c->stream, Fh.c(), vk, et.d(), Z.c(), 40, c->s_small.d());
+  // U = V~ Z~ (Eq. 20)
+  c->fns_U.ensure((size_t)v * vk * sizeof(cplx));
+  gemm64(c, v, vk, vk, 1.0, view(Vt.p, vk, 1), view(Z.p, vk, 1),
+            0.0, view(c->fns_U.p, vk, 1));
+  // rotate B^P (and dipoles): occupied rows/cols unchanged, virtual with U
+  const int n2 = o + vk;
+  const int64_t nn = (int64_t)n * n, nn2 = (int64_t)n2 * n2;
+  auto rotate = [&](const cplx* src, int64_t nmat, DBuf& dst) {
+    dst.ensure((size_t)nmat * nn2 * sizeof(cplx));
+    DBuf tmp;
+    tmp.ensure((size_t)nmat * n * vk * sizeof(cplx));
+    const cplx* U = c->fns_U.c();
+    // oo block copy
+    for (int64_t P = 0; P < nmat; ++P)
+      copyv(c, o, o, 1.0, view(src + P * nn, n, 1),
+                view(dst.c() + P * nn2, n2, 1));
+    // tmp[P][p][b'] = sum_b src[P][p][o+b] U[b][b']   (all rows p)
+    gemm(c, CVSADC_FP64, n, vk, v, 1.0,
+         batched(view(src + o, n, 1), nn), view(U, vk, 1), 0.0,
+         batched(view(tmp.p, vk, 1), (int64_t)n * vk), (int)nmat);
+    // ov block: rows i < o
+    for (int64_t P = 0; P < nmat; ++P)
+      copyv(c, o, vk, 1.0, view(tmp.c() + P * n * vk, vk, 1),
+                view(dst.c() + P * nn2 + o, n2, 1));
+    // vv block: U^H tmp[P][o:][:]
+    gemm(c, CVSADC_FP64, vk, vk, v, 1.0,
+         conj_of(trans(view(U, vk, 1))),
+         batched(view(tmp.c() + (int64_t)o * vk, vk, 1), (int64_t)n * vk), 0.0,
+         batched(view(dst.c() + (int64_t)o * n2 + o, n2, 1), nn2), (int)nmat);
+    // vo block: U^H src[P][o:][:o]
+    gemm(c, CVSADC_FP64, vk, o, v, 1.0, conj_of(trans(view(U, vk, 1))),
+         batched(view(src + (int64_t)o * n, n, 1), nn), 0.0,
+         batched(view(dst.c() + (int64_t)o * n2, n2, 1), nn2), (int)nmat);
+  };
+  DBuf Bn;
+  rotate(c->B.c(), L, Bn);
+  std::swap(c->B.p, Bn.p);
+  std::swap(c->B.bytes, Bn.bytes);
+  if (c->has_dip) {
+    DBuf dn;
+    rotate(c->dip.c(), 3, dn);
+    std::swap(c->dip.p, dn.p);
+    std::swap(c->dip.bytes, dn.bytes);
+  }
+  // new energies: occupied unchanged, virtual = eps~
+  DBuf en;
+  en.ensure((size_t)n2 * sizeof(double));
+  CVS_CUDA(cudaMemcpyAsync(en.p, c->eps.p, o * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream));
+  CVS_CUDA(cudaMemcpyAsync(en.d() + o, et.p, vk * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream));
+  c->sync();
+  std::swap(c->eps.p, en.p);
+  std::swap(c->eps.bytes, en.bytes);
+  c->nvirt = vk;
+}
+
+void set_sizes(cvsadc_ctx* c) {
+  c->o = c->ncore + c->nval;
+  c->n = c->o + c->nvirt;
+  c->N1 = (int64_t)c->ncore * c->nvirt;
+  c->npair = (int64_t)c->nvirt * (c->nvirt - 1) / 2;
+  c->N2 = (int64_t)c->ncore * c->nval * c->npair;
+  c->N = c->N1 + c->N2;
+}
+
+void validate(const cvsadc_params* p) {
+  CVS_REQUIRE(p != nullptr, CVSADC_EINVAL, "params is NULL");
+  CVS_REQUIRE(p->ncore >= 1 && p->nval >= 1 && p->nvirt >= 2 && p->naux >= 1,
+              CVSADC_EINVAL, "partition sizes must be ncore>=1, nval>=1, nvirt>=2, naux>=1");
+  CVS_REQUIRE(p->precision == CVSADC_FP64 || p->precision == CVSADC_MIXED_BF16X3,
+              CVSADC_EINVAL, "unknown precision");
+  int64_t n = (int64_t)p->ncore + p->nval + p->nvirt;
+  int64_t o = (int64_t)p->ncore + p->nval;
+  CVS_REQUIRE(n <= 20000 && (int64_t)p->naux * n * n < (1LL << 40), CVSADC_EINVAL,
+              "problem too large");
+  CVS_REQUIRE(o * p->nvirt * (int64_t)p->nvirt * p->nval < (1LL << 31) * 64LL,
+              CVSADC_EINVAL, "problem too large");
+}
+
+void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
+                  const void* B, const void* dip, cvsadc_info* info) {
+  validate(p);
+  CVS_REQUIRE(eps && B, CVSADC_EINVAL, "eps and B are required");
+  double t0 = now_ms();
+  bool dev = (p->flags & CVSADC_FLAG_DEVICE_PTRS) != 0;
+  c->prepared = false;
+  c->ncore = p->ncore;
+  c->nval = p->nval;
+  c->nvirt_in = c->nvirt = p->nvirt;
+  c->naux = p->naux;
+  set_sizes(c);
+  const int n = c->n;
+  upload(c, c->eps, eps, n * sizeof(double), dev);
+  upload(c, c->B, B, (size_t)c->naux * n * n * sizeof(cplx), dev);
+  c->has_dip = dip != nullptr;
+  if (c->has_dip) upload(c, c->dip, dip, (size_t)3 * n * n * sizeof(cplx), dev);
+  check_hermitian(c, c->B.c(), n, c->naux, "B");
+  if (c->has_dip) check_hermitian(c, c->dip.c(), n, 3, "dip");
+  c->has_fns = p->fns_threshold > 0;
+  int prec = p->precision;
+  if (c->has_fns) {
+    build_fns(c, prec, p->fns_threshold);
+    set_sizes(c);
+  }
+  auto stage = [&](const char* what, double t) {
+    if (verbose()) {
+      c->sync();
+      fprintf(stderr, "[cvsadc] %-8s %10.2f ms\n", what, now_ms() - t);
+    }
+  };
+  double ts = now_ms();
+  build_t2(c, prec, c->B.c(), c->eps.d(), c->o, c->nvirt, c->naux, c->t2, c->g2,
+           &c->emp2);
+  stage("t2", ts);
+  ts = now_ms();
+  build_m11(c, prec);
+  stage("m11", ts);
+  ts = now_ms();
+  if (c->has_dip) build_moments(c, prec);
+  stage("moments", ts);
+  c->diag.ensure(c->N * sizeof(double));
+  build_diag(c->stream, c->M11.c(), c->eps.d(), c->ncore, c->nval, c->nvirt,
+             c->diag.d());
+  c->sync();
+  c->prepared = true;
+  if (info) {
+    info->emp2 = c->emp2;
+    info->nvirt_kept = c->nvirt;
+    info->t_prepare_ms = now_ms() - t0;
+  }
+}
+
+// ------------------------------------------------------------- Davidson
+struct DavResult {
+  int iters = 0, sigmas = 0, converged = 0;
+  double maxres = 0.0;
+};
+
+DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
+                        int max_sub, double tol, const cplx* X0, int nx0,
+                        cplx* Xout, double* wout) {
+  const int64_t N = c->N;
+  const int k = nroots;
+  const int msub = std::max(max_sub, 2 * k + 2);
+  DavResult res;
+  c->dv_V.ensure((size_t)msub * N * sizeof(cplx));
+  c->dv_W.ensure((size_t)msub * N * sizeof(cplx));
+  c->dv_X.ensure((size_t)k * N * sizeof(cplx));
+  c->dv_AX.ensure((size_t)k * N * sizeof(cplx));
+  c->dv_T.ensure((size_t)k * N * sizeof(cplx));
+  c->dv_H.ensure((size_t)msub * msub * sizeof(cplx));
+  c->dv_A.ensure((size_t)msub * msub * sizeof(cplx));
+  c->dv_U.ensure((size_t)msub * msub * sizeof(cplx));
+  c->dv_w.ensure((size_t)(msub + 64) * sizeof(double));
+  // dv_misc: ts_dot partials [msub*msub*TS_CHUNKS] complex, then a
+  // double work area laid out at fixed offsets
+  const size_t W_PART = 0, W_RN2 = 64 * 320, W_JAC = W_RN2 + 128,
+               W_KS = W_JAC + 64, W_IDX = W_KS + 1024, W_COEF = W_IDX + 128,
+               W_TOTAL = W_COEF + 4 * 256;
+  c->dv_misc.ensure((size_t)msub * msub * TS_CHUNKS * sizeof(cplx) +
+                    W_TOTAL * sizeof(double));
+  cplx* V = c->dv_V.c();
+  cplx* W = c->dv_W.c();
+  cplx* part = c->dv_misc.c();
+  double* dwork = (double*)(part + (size_t)msub * msub * TS_CHUNKS);
+  cplx* coef = (cplx*)(dwork + W_COEF);  // up to 512 complex scalars
+  cudaStream_t s = c->stream;
+
+  // initial vectors: given X0, else unit vectors at the smallest diagonal
+  int m = 0;
+  int nguess = std::min<int64_t>(std::max(k, std::min(2 * k, msub / 2)), N);
+  if (X0 && nx0 > 0) {
+    CVS_CUDA(cudaMemcpyAsync(V, X0, (size_t)nx0 * N * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, s));
+    nguess = nx0;
+  } else {
+    nguess = std::min(nguess, 64);
+    int64_t* idx = (int64_t*)(dwork + W_IDX);
+    k_smallest(s, c->diag.d(), N, nguess, idx, dwork + W_KS);
+    std::vector<int64_t> hidx(nguess);
+    CVS_CUDA(cudaMemcpyAsync(hidx.data(), idx, nguess * sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemsetAsync(V, 0, (size_t)nguess * N * sizeof(cplx), s));
+    c->sync();
+    cplx one = cmake(1, 0);
+    for (int q = 0; q < nguess; ++q)
+      CVS_CUDA(cudaMemcpyAsync(V + q * N + hidx[q], &one, sizeof(cplx),
+                               cudaMemcpyHostToDevice, s));
+  }
+  // orthonormalise the starting block (two-pass classical Gram-Schmidt)
+  auto orthonormalise_append = [&](const cplx* src, int cnt) {
+    int added = 0;
+    std::vector<cplx> nrm(1);
+    for (int q = 0; q < cnt; ++q) {
+      cplx* dst = V + (int64_t)m * N;
+      if (dst != src + (int64_t)q * N)
+        CVS_CUDA(cudaMemcpyAsync(dst, src + (int64_t)q * N, N * sizeof(cplx),
+                                 cudaMemcpyDeviceToDevice, s));
+      double n0 = 0;
+      {
+        cplx* out = coef;
+        ts_dot(s, dst, 1, dst, 1, N, part, out, 1);
+        CVS_CUDA(cudaMemcpyAsync(nrm.data(), out, sizeof(cplx),
+                                 cudaMemcpyDeviceToHost, s));
+        c->sync();
+        n0 = std::sqrt(std::max(nrm[0].x, 0.0));
+      }
+      if (m > 0) {
+        for (int pass = 0; pass < 2; ++pass) {
+          cplx* cf = coef;
+          ts_dot(s, V, m, dst, 1, N, part, cf, 1);
+          ts_subtract(s, V, m, cf, 1, 1, N, dst);
+        }
+      }
+      cplx* out = coef;
+      ts_dot(s, dst, 1, dst, 1, N, part, out, 1);
+      CVS_CUDA(cudaMemcpyAsync(nrm.data(), out, sizeof(cplx),
+                               cudaMemcpyDeviceToHost, s));
+      c->sync();
+      double nr = std::sqrt(std::max(nrm[0].x, 0.0));
+      if (nr > 1e-8 * std::max(n0, 1e-300) && nr > 1e-300) {
+        double sc = 1.0 / nr;
+        CVS_CUDA(cudaMemcpyAsync(dwork + W_KS, &sc, sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+        scale_vectors(s, dst, dwork + W_KS, 1, N);
+        c->sync();  // sc lives on the host stack
+        ++m;
+        ++added;
+        if (m >= msub) break;
+      }
+    }
+    return added;
+  };
+  {
+    // guesses live in V already at slots [0, nguess): compact through W
+    CVS_CUDA(cudaMemcpyAsync(W, V, (size_t)nguess * N * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, s));
+    m = 0;
+    orthonormalise_append(W, nguess);
+  }
+  int m_done = 0;  // vectors whose sigma is known
+  std::vector<double> theta(k), rn2(k);
+  std::vector<cplx> hostbuf;
+  for (int it = 0; it < max_iter; ++it) {
+    // sigma for new vectors
+    int nnew = m - m_done;
+    sigma_impl(c, prec, V + (int64_t)m_done * N, W + (int64_t)m_done * N, nnew);
+    res.sigmas += nnew;
+    // subspace matrix columns for the new vectors
+    ts_dot(s, V, m, W + (int64_t)m_done * N, nnew, N, part,
+           c->dv_H.c() + m_done, msub);
+    // rows for the new vectors against old sigma (Hermitian completion is
+    // done from both triangles; fill the remaining block)
+    if (m_done > 0)
+      ts_dot(s, V + (int64_t)m_done * N, nnew, W, m_done, N, part,
+             c->dv_H.c() + (int64_t)m_done * msub, msub);
+    m_done = m;
+    // A = (H + H^H)/2 over m x m (H stored with leading dimension msub)
+    hermitize(s, c->dv_H.c(), msub, m, c->dv_A.c());
+    jacobi_eigh(s, c->dv_A.c(), m, c->dv_w.d(), c->dv_U.c(), 60,
+                dwork + W_JAC);
+    // Ritz vectors and their sigma images for the lowest k
+    ts_combine(s, V, c->dv_U.c(), nullptr, nullptr, m, m, k, N, c->dv_X.c());
+    ts_combine(s, nullptr, nullptr, W, c->dv_U.c(), m, m, k, N, c->dv_AX.c());
+    residual_precond(s, c->dv_AX.c(), c->dv_X.c(), c->dv_w.d(), c->diag.d(),
+                     k, N, c->dv_T.c(), dwork + W_PART, dwork + W_RN2);
+    CVS_CUDA(cudaMemcpyAsync(theta.data(), c->dv_w.d(), k * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemcpyAsync(rn2.data(), dwork + W_RN2, k * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    c->sync();
+    res.iters = it + 1;
+    if (verbose()) {
+      double mx = 0;
+      for (int r = 0; r < k; ++r) mx = std::max(mx, rn2[r]);
+      fprintf(stderr, "[cvsadc] davidson it %3d m %3d theta0 %.12f max|r| %.3e\n",
+              it, m, theta[0], std::sqrt(mx));
+    }
+    std::vector<int> todo;
+    res.maxres = 0;
+    res.converged = 0;
+    for (int r = 0; r < k; ++r) {
+      double rn = std::sqrt(std::max(rn2[r], 0.0));
+      res.maxres = std::max(res.maxres, rn);
+      if (rn <= tol)
+        ++res.converged;
+      else
+        todo.push_back(r);
+    }
+    if (todo.empty() || it == max_iter - 1) break;
+    // restart (thick, to the k Ritz vectors) if the new block does not fit
+    if (m + (int)todo.size() > msub) {
+      CVS_CUDA(cudaMemcpyAsync(V, c->dv_X.p, (size_t)k * N * sizeof(cplx),
+                               cudaMemcpyDeviceToDevice, s));
+      CVS_CUDA(cudaMemcpyAsync(W, c->dv_AX.p, (size_t)k * N * sizeof(cplx),
+                               cudaMemcpyDeviceToDevice, s));
+      // H = diag(theta)
+      std::vector<cplx> h((size_t)msub * msub, cmake(0, 0));
+      for (int r = 0; r < k; ++r) h[(size_t)r * msub + r] = cmake(theta[r], 0);
+      CVS_CUDA(cudaMemcpyAsync(c->dv_H.p, h.data(), h.size() * sizeof(cplx),
+                               cudaMemcpyHostToDevice, s));
+      m = k;
+      m_done = k;
+    }
+    // append corrections of the unconverged roots
+    for (size_t q = 0; q < todo.size(); ++q)
+      if (todo[q] != (int)q)
+        CVS_CUDA(cudaMemcpyAsync(c->dv_T.c() + (int64_t)q * N,
+                                 c->dv_T.c() + (int64_t)todo[q] * N,
+                                 N * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    int added = orthonormalise_append(c->dv_T.c(), (int)todo.size());
+    if (added == 0) break;
+  }
+  CVS_CUDA(cudaMemcpyAsync(wout, c->dv_w.d(), k * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+  CVS_CUDA(cudaMemcpyAsync(Xout, c->dv_X.p, (size_t)k * N * sizeof(cplx),
+                           cudaMemcpyDeviceToDevice, s));
+  c->sync();
+  return res;
+}
+
+void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
+                    void* X, double* osc, cvsadc_info* info) {
+  CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
+  CVS_REQUIRE(omega, CVSADC_EINVAL, "omega is required");
+  const int k = p->nroots;
+  CVS_REQUIRE(k >= 1 && k <= 64 && k <= c->N, CVSADC_EINVAL, "bad nroots");
+  bool dev = (p->flags & CVSADC_FLAG_DEVICE_PTRS) != 0;
+  double tol = p->conv_residual > 0 ? p->conv_residual : 1e-6;
+  int max_iter = p->max_iter > 0 ? p->max_iter : 400;
+  int max_sub = p->max_subspace > 0 ? p->max_subspace : std::max(8 * k, 48);
+  max_sub = std::min(max_sub, 128);
+  double t0 = now_ms();
+  DBuf Xd;
+  Xd.ensure((size_t)k * c->N * sizeof(cplx));
+  std::vector<double> w(k);
+  DavResult r = davidson_impl(c, p->precision, k, max_iter, max_sub, tol,
+                              nullptr, 0, Xd.c(), w.data());
+  double t1 = now_ms();
+  double t_ref = 0;
+  if (p->precision != CVSADC_FP64 && !(p->flags & CVSADC_FLAG_NO_REFINE)) {
+    // FP64 residual correction: Davidson in FP64 started from the
+    // converged mixed-precision Ritz vectors
+    DBuf X0;
+    X0.ensure((size_t)k * c->N * sizeof(cplx));
+    CVS_CUDA(cudaMemcpyAsync(X0.p, Xd.p, (size_t)k * c->N * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, c->stream));
+    DavResult r2 = davidson_impl(c, CVSADC_FP64, k, 20, max_sub, tol, X0.c(), k,
+                                 Xd.c(), w.data());
+    r.iters += r2.iters;
+    r.sigmas += r2.sigmas;
+    r.converged = r2.converged;
+    r.maxres = r2.maxres;
+    t_ref = now_ms() - t1;
+  }
+  phase_fix(c->stream, Xd.c(), k, c->N, c->dv_misc.d());
+  if (dev)
+    CVS_CUDA(cudaMemcpyAsync(omega, w.data(), k * sizeof(double),
+                             cudaMemcpyHostToDevice, c->stream));
+  else
+    std::memcpy(omega, w.data(), k * sizeof(double));
+  if (X && (p->flags & CVSADC_FLAG_RETURN_X))
+    download(c, X, Xd.p, (size_t)k * c->N * sizeof(cplx), dev);
+  if (osc && c->has_dip) {
+    // T_n^x = X_n^H F^x, f_n = 2/3 w_n sum_x |T|^2
+    cplx* part = c->dv_misc.c();
+    cplx* Tn = part + (size_t)k * 3 * TS_CHUNKS;
+    ts_dot(c->stream, Xd.c(), k, c->F.c(), 3, c->N, part, Tn, 3);
+    std::vector<cplx> T((size_t)k * 3);
+    CVS_CUDA(cudaMemcpyAsync(T.data(), Tn, T.size() * sizeof(cplx),
+                             cudaMemcpyDeviceToHost, c->stream));
+    c->sync();
+    std::vector<double> f(k);
+    for (int r0 = 0; r0 < k; ++r0) {
+      double s2 = 0;
+      for (int x = 0; x < 3; ++x) {
+        cplx t = T[(size_t)r0 * 3 + x];
+        s2 += t.x * t.x + t.y * t.y;
+      }
+      f[r0] = 2.0 / 3.0 * w[r0] * s2;
+    }
+    if (dev)
+      CVS_CUDA(cudaMemcpyAsync(osc, f.data(), k * sizeof(double),
+                               cudaMemcpyHostToDevice, c->stream));
+    else
+      std::memcpy(osc, f.data(), k * sizeof(double));
+  }
+  c->sync();
+  if (info) {
+    info->iterations = r.iters;
+    info->sigma_vectors = r.sigmas;
+    info->converged = r.converged;
+    info->max_residual = r.maxres;
+    info->t_davidson_ms = t1 - t0;
+    info->t_refine_ms = t_ref;
+    info->emp2 = c->emp2;
+    info->nvirt_kept = c->nvirt;
+  }
+  if (r.converged < k) throw Error{CVSADC_ENOTCONV, "Davidson did not converge"};
+}
+
+template <typename F>
+int guarded(cvsadc_ctx* c, F&& f) {
+  try {
+    if (c) CVS_CUDA(cudaSetDevice(c->device));
+    f();
+    if (c) c->last_error.clear();
+    return CVSADC_OK;
+  } catch (const Error& e) {
+    if (c) c->last_error = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (c) c->last_error = "host allocation failed";
+    return CVSADC_ENOMEM;
+  } catch (...) {
+    if (c) c->last_error = "unexpected internal error";
+    return CVSADC_ECUDA;
+  }
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+int cvsadc_create(cvsadc_ctx** ctx, int device, void* cuda_stream) {
+  if (!ctx) return CVSADC_EINVAL;
+  *ctx = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return CVSADC_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return CVSADC_EINVAL;
+  cvsadc_ctx* c = new (std::nothrow) cvsadc_ctx();
+  if (!c) return CVSADC_ENOMEM;
+  c->device = device;
+  int rc = guarded(c, [&] {
+    init_kernel_attributes();
+    if (cuda_stream) {
+      c->stream = (cudaStream_t)cuda_stream;
+    } else {
+      CVS_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+      c->own_stream = true;
+    }
+  });
+  if (rc != CVSADC_OK) {
+    delete c;
+    return rc;
+  }
+  *ctx = c;
+  return CVSADC_OK;
+}
+
+void cvsadc_destroy(cvsadc_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* cvsadc_strerror(int status) {
+  switch (status) {
+    case CVSADC_OK: return "ok";
+    case CVSADC_EINVAL: return "invalid argument";
+    case CVSADC_ENONHERM: return "input matrix is not Hermitian";
+    case CVSADC_ENOMEM: return "out of memory";
+    case CVSADC_ECUDA: return "CUDA error";
+    case CVSADC_ETIMEOUT: return "device wait timed out";
+    case CVSADC_ESTATE: return "no prepared problem";
+    case CVSADC_ENOTCONV: return "not converged";
+    default: return "unknown status";
+  }
+}
+
+const char* cvsadc_last_error(cvsadc_ctx* c) {
+  return c ? c->last_error.c_str() : "";
+}
+
+int cvsadc_prepare(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
+                   const void* B, const void* dip, cvsadc_info* info) {
+  if (!c) return CVSADC_EINVAL;
+  return guarded(c, [&] { prepare_impl(c, p, eps, B, dip, info); });
+}
+
+int cvsadc_prepared_sizes(cvsadc_ctx* c, int32_t* nvirt, int64_t* N1,
+                          int64_t* N2) {
+  if (!c) return CVSADC_EINVAL;
+  if (!c->prepared) return CVSADC_ESTATE;
+  if (nvirt) *nvirt = c->nvirt;
+  if (N1) *N1 = c->N1;
+  if (N2) *N2 = c->N2;
+  return CVSADC_OK;
+}
+
+int cvsadc_get_t2(cvsadc_ctx* c, int32_t flags, void* t2, double* emp2) {
+  if (!c) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
+    if (emp2) *emp2 = c->emp2;
+    if (t2)
+      download(c, t2, c->t2.p, (size_t)c->o * c->o * c->nvirt * c->nvirt * sizeof(cplx),
+               flags & CVSADC_FLAG_DEVICE_PTRS);
+    c->sync();
+  });
+}
+
+int cvsadc_get_m11(cvsadc_ctx* c, int32_t flags, void* m11) {
+  if (!c || !m11) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
+    download(c, m11, c->M11.p, (size_t)c->N1 * c->N1 * sizeof(cplx),
+             flags & CVSADC_FLAG_DEVICE_PTRS);
+    c->sync();
+  });
+}
+
+int cvsadc_get_fns(cvsadc_ctx* c, int32_t flags, double* occ, void* U) {
+  if (!c) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    CVS_REQUIRE(c->prepared && c->has_fns, CVSADC_ESTATE, "no FNS in the prepared problem");
+    bool dev = flags & CVSADC_FLAG_DEVICE_PTRS;
+    if (occ) download(c, occ, c->fns_occ.p, c->nvirt_in * sizeof(double), dev);
+    if (U)
+      download(c, U, c->fns_U.p, (size_t)c->nvirt_in * c->nvirt * sizeof(cplx), dev);
+    c->sync();
+  });
+}
+
+int cvsadc_get_moments(cvsadc_ctx* c, int32_t flags, void* F) {
+  if (!c || !F) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    CVS_REQUIRE(c->prepared && c->has_dip, CVSADC_ESTATE, "no dipoles in the prepared problem");
+    download(c, F, c->F.p, (size_t)3 * c->N * sizeof(cplx),
+             flags & CVSADC_FLAG_DEVICE_PTRS);
+    c->sync();
+  });
+}
+
+int cvsadc_sigma(cvsadc_ctx* c, int32_t precision, int32_t flags,
+                 const void* x, void* sigma, int32_t nvec) {
+  if (!c || !x || !sigma || nvec < 0) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
+    CVS_REQUIRE(precision == CVSADC_FP64 || precision == CVSADC_MIXED_BF16X3,
+                CVSADC_EINVAL, "unknown precision");
+    if (nvec == 0) return;
+    bool dev = flags & CVSADC_FLAG_DEVICE_PTRS;
+    size_t bytes = (size_t)nvec * c->N * sizeof(cplx);
+    if (dev) {
+      RegGuard gx(x, bytes), gs(sigma, bytes);
+      sigma_impl(c, precision, (const cplx*)x, (cplx*)sigma, nvec);
+    } else {
+      DBuf xd, sd;
+      xd.ensure(bytes);
+      sd.ensure(bytes);
+      CVS_CUDA(cudaMemcpyAsync(xd.p, x, bytes, cudaMemcpyHostToDevice, c->stream));
+      sigma_impl(c, precision, xd.c(), sd.c(), nvec);
+      CVS_CUDA(cudaMemcpyAsync(sigma, sd.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+      c->sync();
+    }
+    c->sync();
+  });
+}
+
+int cvsadc_davidson(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
+                    void* X, double* osc, cvsadc_info* info) {
+  if (!c || !p) return CVSADC_EINVAL;
+  return guarded(c, [&] { davidson_entry(c, p, omega, X, osc, info); });
+}
+
+int cvsadc_solve(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
+                 const void* B, const void* dip, double* omega, void* X,
+                 double* osc, cvsadc_info* info) {
+  if (!c || !p) return CVSADC_EINVAL;
+  double t0 = now_ms();
+  int rc = guarded(c, [&] { prepare_impl(c, p, eps, B, dip, info); });
+  if (rc != CVSADC_OK) return rc;
+  rc = guarded(c, [&] { davidson_entry(c, p, omega, X, osc, info); });
+  if (info) info->t_total_ms = now_ms() - t0;
+  return rc;
+}
+
+}  // extern "C"

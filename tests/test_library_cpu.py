@@ -1,0 +1,61 @@
+"""Host-side checks of the C-ABI library: it builds, loads, and exports
+every entry point declared in include/cvsadc.h.  No compute calls (there
+is no GPU here)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "cvsadc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cvsadc_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_27451_gb300 import _lib, build
+
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("cvsadc_create", "cvsadc_destroy", "cvsadc_solve",
+                 "cvsadc_strerror", "cvsadc_sigma", "cvsadc_prepare"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    from paper_2604_27451_gb300 import _lib
+
+    assert sorted(_lib.exported_names()) == _declared()
+
+
+def test_strerror_and_null_arguments(lib):
+    assert lib.cvsadc_strerror(0) == b"ok"
+    assert lib.cvsadc_strerror(-2).startswith(b"input matrix")
+    assert lib.cvsadc_create(None, 0, None) == -1
+    # NULL context is rejected without touching the device
+    assert lib.cvsadc_solve(None, None, None, None, None, None, None, None, None) == -1
+    assert lib.cvsadc_sigma(None, 0, 0, None, None, 1) == -1
+    lib.cvsadc_destroy(None)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = lib.cvsadc_create(ctypes.byref(h), 0, None)
+    assert rc in (-1, -4)
+    assert not h.value
