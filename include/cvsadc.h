@@ -62,11 +62,23 @@ extern "C" {
 
 /* ----------------------------------------------------------- precision */
 #define CVSADC_FP64 0          /* complex128 throughout, FP64 FMA GEMMs */
-#define CVSADC_MIXED_BF16X3 1  /* GEMMs on tcgen05 tensor cores with
-                                  3-term bf16 splits and FP32 accumulation;
-                                  denominators, Gram-Schmidt, norms,
-                                  subspace eigensolve and the final residual
-                                  correction in FP64 */
+#define CVSADC_MIXED_BF16X3 1  /* GEMMs on tcgen05 tensor cores: each real
+                                  value split into bf16 hi + lo, three
+                                  products kept, FP32 accumulation in
+                                  tensor memory; the accumulation limits the
+                                  error to ~1e-5 relative at K ~ 10^3-10^4 */
+#define CVSADC_MIXED_SLICE4 2  /* tensor-core GEMMs on exact integer slices:
+                                  per-row/column power-of-two scales, four
+                                  7-bit slices per value (10 slice products),
+                                  exact FP32 runs of <= 1024 products drained
+                                  to float-float accumulators: error ~2^-28
+                                  of (row max x column max) */
+#define CVSADC_FP64_SLICE7 3   /* as SLICE4 with seven slices (28 products):
+                                  FP64-class accuracy on the tensor cores.
+                                  In all mixed modes the denominators,
+                                  Gram-Schmidt, norms, subspace eigensolve
+                                  and the final residual correction run in
+                                  FP64 */
 
 /* ---------------------------------------------------------------- flags */
 #define CVSADC_FLAG_DEVICE_PTRS 1  /* array arguments are device pointers */
@@ -77,14 +89,20 @@ extern "C" {
 typedef struct {
   int32_t ncore, nval, nvirt, naux;
   int32_t nroots;         /* lowest nroots eigenvalues of the CVS-ADC(2) matrix */
-  int32_t precision;      /* CVSADC_FP64 or CVSADC_MIXED_BF16X3 */
+  int32_t precision;      /* CVSADC_FP64, _MIXED_BF16X3, _MIXED_SLICE4,
+                             _FP64_SLICE7 */
   double fns_threshold;   /* tau for frozen natural spinors; <= 0 keeps all virtuals */
   double conv_residual;   /* Davidson convergence, 2-norm of M x - w x; default 1e-6 */
   int32_t max_iter;       /* default 400: roots dominated by strongly coupled
                              doubles can take a few hundred iterations */
   int32_t max_subspace;   /* default max(8 nroots, 48) */
   int32_t flags;          /* CVSADC_FLAG_* */
-  int32_t reserved;
+  int32_t refine_sweeps;  /* mixed precision: FP64 residual-correction
+                             iterations after the mixed Davidson (which stops
+                             at max(conv_residual, 3e-4) for BF16X3 and
+                             max(conv_residual, 1e-6) for SLICE4); each
+                             costs one FP64 sigma per unconverged root;
+                             default 2 */
 } cvsadc_params;
 
 typedef struct {
@@ -173,11 +191,23 @@ int cvsadc_get_fns(cvsadc_ctx* ctx, int32_t flags, double* occ, void* U);
 int cvsadc_get_moments(cvsadc_ctx* ctx, int32_t flags, void* F);
 
 /* sigma = M x for nvec CVS-packed vectors x [nvec][N] complex, written to
- * sigma [nvec][N].  precision: CVSADC_FP64 or CVSADC_MIXED_BF16X3 (the
+ * sigma [nvec][N].  precision: any CVSADC_FP64 / CVSADC_MIXED_* (the
  * couplings M12 and M21 are contracted through B^P; M22 is applied on the
  * fly; M11 x1 is a dense product). */
 int cvsadc_sigma(cvsadc_ctx* ctx, int32_t precision, int32_t flags,
                  const void* x, void* sigma, int32_t nvec);
+
+/* Plain complex GEMM with the library's engines: C = A B for row-major
+ * complex matrices A [M][lda], B [K][ldb], C [M][ldc] (interleaved
+ * complex128).  precision CVSADC_FP64 runs the FP64 FMA kernel;
+ * the mixed modes the tcgen05 kernels (see the precision constants) when
+ * the product is large enough to pay for its operand packing, else the
+ * FP64 kernel.  Memory space per `flags`.  Errors:
+ * EINVAL (sizes, leading dimensions), ETIMEOUT (a bounded device wait of
+ * the tensor-core kernel expired), ENOMEM, ECUDA. */
+int cvsadc_zgemm(cvsadc_ctx* ctx, int32_t precision, int32_t flags,
+                 int32_t M, int32_t N, int32_t K, const void* A, int64_t lda,
+                 const void* B, int64_t ldb, void* C, int64_t ldc);
 
 /* Davidson on the prepared problem (see cvsadc_solve for outputs). */
 int cvsadc_davidson(cvsadc_ctx* ctx, const cvsadc_params* params,

@@ -20,7 +20,7 @@ from ._lib import (  # noqa: F401
 )
 
 PRECISIONS = {"fp64": CVSADC_FP64, "bf16x3": CVSADC_MIXED_BF16X3,
-              "mixed": CVSADC_MIXED_BF16X3}
+              "slice4": 2, "fp64_slice7": 3}
 
 
 class CvsadcError(RuntimeError):
@@ -80,7 +80,8 @@ class Context:
     # ------------------------------------------------------------ params
     @staticmethod
     def params(ncore, nval, nvirt, naux, nroots=4, precision="fp64",
-               tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, flags=0):
+               tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, flags=0,
+               refine_sweeps=0):
         p = Params()
         p.ncore, p.nval, p.nvirt, p.naux = ncore, nval, nvirt, naux
         p.nroots = nroots
@@ -90,6 +91,7 @@ class Context:
         p.max_iter = max_iter
         p.max_subspace = max_subspace
         p.flags = flags
+        p.refine_sweeps = refine_sweeps
         return p
 
     # ----------------------------------------------------------- stages
@@ -162,6 +164,25 @@ class Context:
         self._check(self.lib.cvsadc_sigma(self.h, prec, flags, px, po, nvec))
         return out
 
+    def zgemm(self, A, B, precision="fp64"):
+        """C = A B (complex) with the library's GEMM engines."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        M, K = A.shape
+        K2, N = B.shape
+        assert K == K2
+        pa, dev = _ptr(A)
+        pb, _ = _ptr(B)
+        if dev:
+            import torch
+            C = torch.empty((M, N), dtype=A.dtype, device=A.device)
+        else:
+            C = np.empty((M, N), dtype=np.complex128)
+        pc, _ = _ptr(C)
+        flags = CVSADC_FLAG_DEVICE_PTRS if dev else 0
+        self._check(self.lib.cvsadc_zgemm(self.h, prec, flags, M, N, K, pa, K, pb, N,
+                                          pc, N))
+        return C
+
     def davidson(self, nroots, precision="fp64", conv=1e-6, max_iter=0,
                  max_subspace=0, return_x=False, refine=True):
         s = self._shape
@@ -181,16 +202,18 @@ class Context:
         return dict(omega=omega, osc=osc, X=X, info=info.as_dict(), status=rc)
 
     def solve(self, eps, B, dip, ncore, nval, nvirt, nroots, precision="fp64",
-              tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, return_x=False):
+              tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, return_x=False,
+              refine=True, refine_sweeps=0):
         """The whole path through cvsadc_solve."""
         naux = B.shape[0]
         pe, dev = _ptr(eps)
         pb, _ = _ptr(B)
         pd, _ = _ptr(dip)
         flags = (CVSADC_FLAG_DEVICE_PTRS if dev else 0) | \
-            (CVSADC_FLAG_RETURN_X if return_x else 0)
+            (CVSADC_FLAG_RETURN_X if return_x else 0) | \
+            (0 if refine else CVSADC_FLAG_NO_REFINE)
         p = self.params(ncore, nval, nvirt, naux, nroots, precision, tau, conv,
-                        max_iter, max_subspace, flags)
+                        max_iter, max_subspace, flags, refine_sweeps)
         if dev:
             import torch
             omega = torch.empty(nroots, dtype=torch.float64, device=eps.device)

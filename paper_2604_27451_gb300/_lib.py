@@ -24,6 +24,8 @@ CVSADC_ENOTCONV = 1
 
 CVSADC_FP64 = 0
 CVSADC_MIXED_BF16X3 = 1
+CVSADC_MIXED_SLICE4 = 2
+CVSADC_FP64_SLICE7 = 3
 
 CVSADC_FLAG_DEVICE_PTRS = 1
 CVSADC_FLAG_RETURN_X = 2
@@ -37,7 +39,7 @@ class Params(ctypes.Structure):
         ("nroots", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("fns_threshold", ctypes.c_double), ("conv_residual", ctypes.c_double),
         ("max_iter", ctypes.c_int32), ("max_subspace", ctypes.c_int32),
-        ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("refine_sweeps", ctypes.c_int32),
     ]
 
 
@@ -75,6 +77,9 @@ _SIGNATURES = {
                                     ctypes.c_int32]),
     "cvsadc_davidson": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp,
                                        ctypes.POINTER(Info)]),
+    "cvsadc_zgemm": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64,
+                                    _vp, ctypes.c_int64, _vp, ctypes.c_int64]),
 }
 
 _lib = None

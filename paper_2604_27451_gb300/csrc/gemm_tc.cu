@@ -1,16 +1,874 @@
-// tcgen05 tensor-core complex GEMM (placeholder until the kernel lands).
+// Complex GEMM on the 5th-generation tensor cores (tcgen05, sm_103a).
+//
+//   C = alpha * A * B + beta * C, A: M x K, B: K x N complex (two-mode
+//   views), C complex128.
+//
+// Precision: every real value x is split into bfloat16 parts x = x_h + x_l
+// (x_h = bf16(x), x_l = bf16(x - x_h)); a real product keeps x_h y_h +
+// x_h y_l + x_l y_h (~2^-16 relative), accumulated in FP32 in tensor
+// memory.  The tensor-memory accumulation rounds each MMA step, so its
+// error grows linearly with K (measured: ~1e-5 relative at K' ~ 10^4); the
+// exact-slice kernel further down removes that limit.
+//
+// Layout: one real GEMM computes the complex product.  For every product
+// term p = (pa, pb) the K dimension carries two segments of length Kp:
+//   A row m       : [ re_pa(a) , im_pa(a) ]
+//   B' row 2n     : [ re_pb(b) , -im_pb(b) ]   -> column 2n   = Re(a b)
+//   B' row 2n + 1 : [ im_pb(b) ,  re_pb(b) ]   -> column 2n+1 = Im(a b)
+// so K' = 2 * (number of product terms) * Kp and N' = 2 N, with real and
+// imaginary parts of one output
+// element in adjacent accumulator columns.  Packing (split + transpose into
+// K-major rows, zero padding to the tile grid) is a bandwidth kernel; the
+// GEMM itself is TMA -> shared memory (128B swizzle) -> tcgen05.mma with
+// the accumulator in tensor memory -> tcgen05.ld -> complex128 epilogue.
+//
+// CTA: 128 threads.  Thread 0 issues the TMA loads, thread 32 issues the
+// MMAs, all four warps drain TMEM (warp w owns TMEM lanes 32w..32w+31).
+// Every mbarrier wait is bounded by a globaltimer deadline; on expiry the
+// kernel records an error code, releases its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace cvs {
 
-bool tc_available() { return false; }
+namespace {
 
-size_t tc_workspace_bytes(int, int, int) { return 0; }
+constexpr int BM = 128;   // UMMA M
+constexpr int BN = 256;   // UMMA N (real columns = 128 complex columns)
+constexpr int BK = 64;    // bf16 elements per 128-byte swizzle row
+constexpr int STAGES = 4;
+constexpr int A_TILE = BM * BK * 2;
+constexpr int B_TILE = BN * BK * 2;
+constexpr int STAGE_BYTES = A_TILE + B_TILE;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint64_t WAIT_NS = 4000000000ull;  // 4 s bound on any wait
 
-void zgemm_tc(cudaStream_t, int, int, int, double, View, View, double, View,
-              void*, size_t) {
-  throw Error{-1, "tensor-core GEMM not available"};
+// product tables: (part of A, part of B), part 0 = hi, 1 = mid/lo, 2 = lo
+template <int NP>
+struct Split;
+template <>
+struct Split<3> {
+  static constexpr int parts = 2;
+  __device__ static int pa(int p) { return p == 2 ? 1 : 0; }
+  __device__ static int pb(int p) { return p == 1 ? 1 : 0; }
+};
+template <>
+struct Split<6> {
+  static constexpr int parts = 3;
+  // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+  __device__ static int pa(int p) {
+    return p == 2 ? 1 : p == 4 ? 1 : p == 5 ? 2 : 0;
+  }
+  __device__ static int pb(int p) {
+    return p == 1 ? 1 : p == 3 ? 2 : p == 4 ? 1 : 0;
+  }
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait on the phase with the given parity
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  uint64_t t0 = gtime();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (gtime() - t0 > WAIT_NS) return false;
+    __nanosleep(64);
+  }
+}
+__device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar,
+                                         void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::"
+      "bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row atoms of
+// 1024 bytes stacked along M/N (stride 1024 B)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+// instruction descriptor, kind::f16: D f32, A/B bf16, both K-major
+__device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t dtm, uint64_t a, uint64_t b,
+                                     uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dtm),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 "
+      "[%0];" ::"r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]),
+        "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]),
+        "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
+                   const __grid_constant__ CUtensorMap tmB, int nkt, int M,
+                   int N, double alpha, double beta, View C, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_TILE;
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tslot = (uint32_t*)(done + 1);
+  __shared__ int fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+  if (threadIdx.x == 0) {
+    fail = 0;
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_u32(tslot)),
+        "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (threadIdx.x == 0) {
+    // TMA producer
+    for (int kt = 0; kt < nkt; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (kt / STAGES) & 1;
+      if (kt >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+        fail = 1;
+        break;
+      }
+      if (fail) break;
+      mbar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load(&tmA, &full[s], sA + s * A_TILE, kt * BK, m0);
+      tma_load(&tmB, &full[s], sB + s * B_TILE, kt * BK, n0);
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    const uint32_t id = idesc_bf16(BM, BN);
+    int kt = 0;
+    for (; kt < nkt; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (kt / STAGES) & 1;
+      if (!mbar_wait(&full[s], ph)) {
+        fail = 2;
+        break;
+      }
+      fence_after();
+      const uint64_t ad = sdesc(smem_u32(sA + s * A_TILE));
+      const uint64_t bd = sdesc(smem_u32(sB + s * B_TILE));
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        umma(tmem, ad + 2 * kk, bd + 2 * kk, id, (kt | kk) ? 1u : 0u);
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0);
+  __syncwarp();
+  fence_after();
+  if (ok && !fail) {
+    const int m = m0 + warp * 32 + lane;
+    const int64_t ro = m < M ? vrow(C, m) : 0;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 16) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+      if (m < M) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int n = (n0 + c) / 2 + q;
+          if (n < N) {
+            cplx* d = C.p + ro + vcol(C, n);
+            cplx o = cmake(alpha * (double)v[2 * q], alpha * (double)v[2 * q + 1]);
+            if (beta != 0.0) {
+              cplx old = *d;
+              o.x += beta * old.x;
+              o.y += beta * old.y;
+            }
+            *d = o;
+          }
+        }
+      }
+    }
+  } else if (lane == 0) {
+    atomicExch(err, fail ? fail : 3);
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
+                     tmem),
+                 "r"(BN));
+}
+
+// ------------------------------------------------------------ packing
+template <int PARTS>
+__device__ __forceinline__ void split(double x, __nv_bfloat16* p) {
+  double r = x;
+#pragma unroll
+  for (int q = 0; q < PARTS; ++q) {
+    __nv_bfloat16 h = __double2bfloat16(r);
+    p[q] = h;
+    r -= (double)__bfloat162float(h);
+  }
+}
+
+// A' [Mp][2 NP Kp]: row m, segment 2p + {0: re, 1: im} of part pa(p)
+template <int NP>
+__global__ void pack_a_kernel(View A, int M, int K, int Mp, int Kp,
+                              __nv_bfloat16* out) {
+  constexpr int PARTS = Split<NP>::parts;
+  const int64_t ld = (int64_t)2 * NP * Kp;
+  const int64_t total = (int64_t)Mp * Kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int m = idx / Kp, k = idx % Kp;
+    cplx a = cmake(0, 0);
+    if (m < M && k < K) {
+      a = A.p[vrow(A, m) + vcol(A, k)];
+      if (A.conj) a.y = -a.y;
+    }
+    __nv_bfloat16 re[PARTS], im[PARTS];
+    split<PARTS>(a.x, re);
+    split<PARTS>(a.y, im);
+    __nv_bfloat16* o = out + (int64_t)m * ld + k;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      o[(2 * p) * (int64_t)Kp] = re[Split<NP>::pa(p)];
+      o[(2 * p + 1) * (int64_t)Kp] = im[Split<NP>::pa(p)];
+    }
+  }
+}
+
+// B' [Np2][2 NP Kp]: rows 2n (real part column) and 2n+1 (imaginary)
+template <int NP>
+__global__ void pack_b_kernel(View B, int K, int N, int Np2, int Kp,
+                              __nv_bfloat16* out) {
+  constexpr int PARTS = Split<NP>::parts;
+  const int64_t ld = (int64_t)2 * NP * Kp;
+  const int64_t total = (int64_t)(Np2 / 2) * Kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int n = idx / Kp, k = idx % Kp;
+    cplx b = cmake(0, 0);
+    if (n < N && k < K) {
+      b = B.p[vrow(B, k) + vcol(B, n)];
+      if (B.conj) b.y = -b.y;
+    }
+    __nv_bfloat16 re[PARTS], im[PARTS];
+    split<PARTS>(b.x, re);
+    split<PARTS>(b.y, im);
+    __nv_bfloat16* o0 = out + (int64_t)(2 * n) * ld + k;
+    __nv_bfloat16* o1 = o0 + ld;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int q = Split<NP>::pb(p);
+      o0[(2 * p) * (int64_t)Kp] = re[q];
+      o0[(2 * p + 1) * (int64_t)Kp] = __hneg(im[q]);
+      o1[(2 * p) * (int64_t)Kp] = im[q];
+      o1[(2 * p + 1) * (int64_t)Kp] = re[q];
+    }
+  }
+}
+
+// ------------------------------------------------------- host helpers
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
+                                  void*, const cuuint64_t*, const cuuint64_t*,
+                                  const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+CUtensorMap make_map(const void* base, int64_t rows, int64_t cols_bf16,
+                     int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  CVS_REQUIRE(fn, -4, "cuTensorMapEncodeTiled unavailable");
+  CUtensorMap m;
+  cuuint64_t dims[2] = {(cuuint64_t)cols_bf16, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols_bf16 * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+                  dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CVS_REQUIRE(r == CUDA_SUCCESS, -4, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+struct Dims {
+  int Mp, Np2, Kp, nseg;
+  size_t a_bytes, b_bytes;
+};
+Dims dims_of(int M, int N, int K, int nprod) {
+  Dims d;
+  d.Mp = (M + BM - 1) / BM * BM;
+  d.Np2 = (2 * N + BN - 1) / BN * BN;
+  d.Kp = (K + BK - 1) / BK * BK;
+  d.nseg = 2 * nprod;
+  d.a_bytes = (size_t)d.Mp * d.nseg * d.Kp * 2;
+  d.b_bytes = (size_t)d.Np2 * d.nseg * d.Kp * 2;
+  return d;
+}
+
+}  // namespace
+
+bool tc_available() {
+  static int avail = -1;
+  if (avail < 0) {
+    int dev = 0, major = 0, minor = 0;
+    avail = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) ==
+            cudaSuccess &&
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) ==
+            cudaSuccess)
+      avail = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+    (void)cudaGetLastError();
+    if (avail)
+      cudaFuncSetAttribute(tc_gemm_kernel,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           SMEM_BYTES);
+  }
+  return avail == 1;
+}
+
+size_t tc_workspace_bytes(int M, int N, int K, int nprod) {
+  Dims d = dims_of(M, N, K, nprod);
+  return d.a_bytes + d.b_bytes + 256;
+}
+
+void zgemm_tc(cudaStream_t s, int nprod, int M, int N, int K, double alpha,
+              View A, View B, double beta, View C, void* work,
+              size_t work_bytes, int* err) {
+  if (M <= 0 || N <= 0) return;
+  CVS_REQUIRE(nprod == 3 || nprod == 6, -1, "zgemm_tc: nprod must be 3 or 6");
+  Dims d = dims_of(M, N, K, nprod);
+  CVS_REQUIRE(work_bytes >= d.a_bytes + d.b_bytes + 256, -1,
+              "zgemm_tc: workspace too small");
+  CVS_REQUIRE(d.Kp > 0, -1, "zgemm_tc: K must be positive");
+  __nv_bfloat16* ap = (__nv_bfloat16*)work;
+  __nv_bfloat16* bp = (__nv_bfloat16*)((char*)work + d.a_bytes);
+  const unsigned ga = grid1d((int64_t)d.Mp * d.Kp, 256);
+  const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * d.Kp, 256);
+  if (nprod == 3) {
+    pack_a_kernel<3><<<ga, 256, 0, s>>>(A, M, K, d.Mp, d.Kp, ap);
+    CVS_CHECK_LAUNCH();
+    pack_b_kernel<3><<<gb, 256, 0, s>>>(B, K, N, d.Np2, d.Kp, bp);
+  } else {
+    pack_a_kernel<6><<<ga, 256, 0, s>>>(A, M, K, d.Mp, d.Kp, ap);
+    CVS_CHECK_LAUNCH();
+    pack_b_kernel<6><<<gb, 256, 0, s>>>(B, K, N, d.Np2, d.Kp, bp);
+  }
+  CVS_CHECK_LAUNCH();
+  CUtensorMap ma = make_map(ap, d.Mp, (int64_t)d.nseg * d.Kp, BM);
+  CUtensorMap mb = make_map(bp, d.Np2, (int64_t)d.nseg * d.Kp, BN);
+  const int nkt = d.nseg * d.Kp / BK;
+  dim3 grid(d.Np2 / BN, d.Mp / BM);
+  tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, nkt, M, N, alpha, beta,
+                                               C, err);
+  CVS_CHECK_LAUNCH();
+}
+
+
+// ===========================================================================
+// Exact-accumulation slice GEMM (an error-free splitting in the manner of
+// Ozaki et al., Numer. Algorithms 59 (2012), mapped onto tcgen05).
+//
+// Every row m of A' and every output column n of B' gets a power-of-two
+// scale 2^e with max |entry| < 2^e.  A scaled value a in (-1, 1) is cut into
+// integer slices q_i in [-128, 128] with a = sum_i q_i 2^{-7(i+1)} + r,
+// |r| <= 2^{-7 s - 1}; each slice is exactly a bf16.  A product of slices is
+// an integer with |q q'| <= 2^14, so a run of up to 1024 products sums
+// exactly in the FP32 tensor-memory accumulator (< 2^24).  Slice products
+// (i, j) with i + j <= s - 1 are kept and grouped so that a run never mixes
+// two (i, j) pairs; each finished run is drained from tensor memory (two
+// accumulator buffers, so draining overlaps the next run) and added, times
+// 2^{-7(i+j+2)}, to float-float accumulators (about 48 bits) in registers.
+// The epilogue applies 2^{e_m + f_n}, alpha and beta in FP64.
+//
+// CTA: 576 threads.  Warp 0 lane 0: TMA producer; warp 1 lane 0: MMA
+// issuer; warps 2..17: drain (warp w reads TMEM lanes 32 (w % 4) .. +31 and
+// the 32 columns [32 c, 32 c + 32), c = (w - 2) / 4, of a 128 x 128 tile).
+// ===========================================================================
+namespace {
+
+constexpr int SBN = 128;          // N' per CTA (64 complex columns)
+constexpr int SSTAGES = 6;
+constexpr int S_A_TILE = BM * BK * 2;
+constexpr int S_B_TILE = SBN * BK * 2;
+constexpr int S_STAGE = S_A_TILE + S_B_TILE;
+constexpr int S_SMEM = SSTAGES * S_STAGE + 1024 + 512;
+constexpr int RUN_KT = 16;         // k-tiles per exact run: 16 * 64 = 1024 terms
+constexpr int SLICE_BITS = 7;
+constexpr int MAX_PAIRS = 36;
+
+__constant__ int c_si[MAX_PAIRS];  // slice of A for pair p
+__constant__ int c_sj[MAX_PAIRS];  // slice of B for pair p
+
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  // TwoSum without contraction
+  float s = __fadd_rn(hi, x);
+  float bp = __fsub_rn(s, hi);
+  float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+__global__ void __launch_bounds__(576, 1)
+    tc_slice_kernel(const __grid_constant__ CUtensorMap tmA,
+                    const __grid_constant__ CUtensorMap tmB, int npairs,
+                    int ktpp, int M, int N, const int* __restrict__ eA,
+                    const int* __restrict__ eB, double alpha, double beta,
+                    View C, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + SSTAGES * S_A_TILE;
+  uint64_t* full = (uint64_t*)(smem + SSTAGES * S_STAGE);
+  uint64_t* empty = full + SSTAGES;
+  uint64_t* afull = empty + SSTAGES;  // [2]
+  uint64_t* aempty = afull + 2;       // [2]
+  uint32_t* tslot = (uint32_t*)(aempty + 2);
+  __shared__ int fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * SBN;
+  const int runs_pp = (ktpp + RUN_KT - 1) / RUN_KT;
+  const int nruns = npairs * runs_pp;
+
+  if (threadIdx.x == 0) {
+    fail = 0;
+    for (int s = 0; s < SSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&afull[b], 1);
+      mbar_init(&aempty[b], 16);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_u32(tslot)),
+        "r"(2 * SBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (threadIdx.x == 0) {
+    // TMA producer over every k-tile of every pair
+    const int nkt = npairs * ktpp;
+    for (int kt = 0; kt < nkt; ++kt) {
+      const int s = kt % SSTAGES;
+      const uint32_t ph = (kt / SSTAGES) & 1;
+      if (kt >= SSTAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+        fail = 1;
+        break;
+      }
+      if (fail) break;
+      mbar_expect_tx(&full[s], S_STAGE);
+      tma_load(&tmA, &full[s], sA + s * S_A_TILE, kt * BK, m0);
+      tma_load(&tmB, &full[s], sB + s * S_B_TILE, kt * BK, n0);
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer: one exact run per (pair, run) into alternating buffers
+    const uint32_t id = idesc_bf16(BM, SBN);
+    int kt = 0;
+    for (int r = 0; r < nruns && !fail; ++r) {
+      const int p = r / runs_pp, rr = r % runs_pp;
+      const int kt0 = p * ktpp + rr * RUN_KT;
+      const int kt1 = min(p * ktpp + ktpp, kt0 + RUN_KT);
+      const int b = r & 1;
+      if (r >= 2 && !mbar_wait(&aempty[b], ((r >> 1) + 1) & 1)) {
+        fail = 4;
+        break;
+      }
+      fence_after();
+      const uint32_t dt = tmem + (uint32_t)(b * SBN);
+      for (kt = kt0; kt < kt1; ++kt) {
+        const int s = kt % SSTAGES;
+        const uint32_t ph = (kt / SSTAGES) & 1;
+        if (!mbar_wait(&full[s], ph)) {
+          fail = 2;
+          break;
+        }
+        fence_after();
+        const uint64_t ad = sdesc(smem_u32(sA + s * S_A_TILE));
+        const uint64_t bd = sdesc(smem_u32(sB + s * S_B_TILE));
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk)
+          umma(dt, ad + 2 * kk, bd + 2 * kk, id, (kt != kt0 || kk) ? 1u : 0u);
+        umma_commit(&empty[s]);
+      }
+      umma_commit(&afull[b]);
+    }
+  } else if (warp >= 2) {
+    // drain warps
+    const int q = warp & 3;            // TMEM lane quarter
+    const int cq = (warp - 2) >> 2;     // 32-column quarter of the tile
+    float hi[32], lo[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0.f;
+    bool ok = true;
+    for (int r = 0; r < nruns; ++r) {
+      const int p = r / runs_pp;
+      const int b = r & 1;
+      if (!mbar_wait(&afull[b], (r >> 1) & 1)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      const float sc = exp2f(-(float)(SLICE_BITS * (c_si[p] + c_sj[p] + 2)));
+      const uint32_t base = tmem + ((uint32_t)(q * 32) << 16) +
+                            (uint32_t)(b * SBN + cq * 32);
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2) {
+        float v[16];
+        tmem_ld16(base + 16 * c2, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          ff_add(hi[16 * c2 + i], lo[16 * c2 + i], v[i] * sc);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                         smem_u32(&aempty[b]))
+                     : "memory");
+      }
+    }
+    if (!ok || fail) {
+      if (lane == 0) atomicExch(err, fail ? fail : 3);
+    } else {
+      const int m = m0 + q * 32 + lane;
+      if (m < M) {
+        const int64_t ro = vrow(C, m);
+        const double em = ldexp(1.0, eA[m]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int n = (n0 + cq * 32) / 2 + i;
+          if (n < N) {
+            const double s = alpha * em * ldexp(1.0, eB[n]);
+            cplx* d = C.p + ro + vcol(C, n);
+            cplx o = cmake(s * ((double)hi[2 * i] + (double)lo[2 * i]),
+                           s * ((double)hi[2 * i + 1] + (double)lo[2 * i + 1]));
+            if (beta != 0.0) {
+              cplx old = *d;
+              o.x += beta * old.x;
+              o.y += beta * old.y;
+            }
+            *d = o;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(
+                     tmem),
+                 "r"(2 * SBN));
+}
+
+// per-row (A: rows m, max over k) exponent: max |re|, |im| < 2^e
+__global__ void row_exp_kernel(View A, int M, int K, int* e) {
+  for (int m = blockIdx.x; m < M; m += gridDim.x) {
+    double mx = 0.0;
+    const int64_t ro = vrow(A, m);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      cplx a = A.p[ro + vcol(A, k)];
+      mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) e[m] = red[0] > 0 ? ilogb(red[0]) + 1 : 0;
+    __syncthreads();
+  }
+}
+
+// per-column (B: columns n, max over k) exponent
+__global__ void col_exp_kernel(View B, int K, int N, int* e) {
+  for (int n = blockIdx.x; n < N; n += gridDim.x) {
+    double mx = 0.0;
+    const int64_t co = vcol(B, n);
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      cplx b = B.p[vrow(B, k) + co];
+      mx = fmax(mx, fmax(fabs(b.x), fabs(b.y)));
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) e[n] = red[0] > 0 ? ilogb(red[0]) + 1 : 0;
+    __syncthreads();
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void slices(double x, int e, __nv_bfloat16* q) {
+  double t = ldexp(x, -e);
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    t *= (double)(1 << SLICE_BITS);
+    double r = rint(t);
+    q[i] = __double2bfloat16(r);  // |r| <= 128: exact
+    t -= r;
+  }
+}
+
+template <int S>
+__global__ void slice_pack_a(View A, int M, int K, int Mp, int Kp, int npairs,
+                             const int* __restrict__ eA, __nv_bfloat16* out) {
+  const int64_t ld = (int64_t)2 * npairs * Kp;
+  const int64_t total = (int64_t)Mp * Kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int m = idx / Kp, k = idx % Kp;
+    cplx a = cmake(0, 0);
+    int e = 0;
+    if (m < M) {
+      e = eA[m];
+      if (k < K) {
+        a = A.p[vrow(A, m) + vcol(A, k)];
+        if (A.conj) a.y = -a.y;
+      }
+    }
+    __nv_bfloat16 re[S], im[S];
+    slices<S>(a.x, e, re);
+    slices<S>(a.y, e, im);
+    __nv_bfloat16* o = out + (int64_t)m * ld + k;
+    for (int p = 0; p < npairs; ++p) {
+      o[(2 * p) * (int64_t)Kp] = re[c_si[p]];
+      o[(2 * p + 1) * (int64_t)Kp] = im[c_si[p]];
+    }
+  }
+}
+
+template <int S>
+__global__ void slice_pack_b(View B, int K, int N, int Np2, int Kp, int npairs,
+                             const int* __restrict__ eB, __nv_bfloat16* out) {
+  const int64_t ld = (int64_t)2 * npairs * Kp;
+  const int64_t total = (int64_t)(Np2 / 2) * Kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int n = idx / Kp, k = idx % Kp;
+    cplx b = cmake(0, 0);
+    int e = 0;
+    if (n < N) {
+      e = eB[n];
+      if (k < K) {
+        b = B.p[vrow(B, k) + vcol(B, n)];
+        if (B.conj) b.y = -b.y;
+      }
+    }
+    __nv_bfloat16 re[S], im[S];
+    slices<S>(b.x, e, re);
+    slices<S>(b.y, e, im);
+    __nv_bfloat16* o0 = out + (int64_t)(2 * n) * ld + k;
+    __nv_bfloat16* o1 = o0 + ld;
+    for (int p = 0; p < npairs; ++p) {
+      const int j = c_sj[p];
+      o0[(2 * p) * (int64_t)Kp] = re[j];
+      o0[(2 * p + 1) * (int64_t)Kp] = __hneg(im[j]);
+      o1[(2 * p) * (int64_t)Kp] = im[j];
+      o1[(2 * p + 1) * (int64_t)Kp] = re[j];
+    }
+  }
+}
+
+struct SDims {
+  int Mp, Np2, Kp, npairs;
+  size_t a_bytes, b_bytes, e_bytes;
+};
+SDims sdims_of(int M, int N, int K, int nslices) {
+  SDims d;
+  d.Mp = (M + BM - 1) / BM * BM;
+  d.Np2 = (2 * N + SBN - 1) / SBN * SBN;
+  d.Kp = (K + BK - 1) / BK * BK;
+  d.npairs = nslices * (nslices + 1) / 2;
+  d.a_bytes = (size_t)d.Mp * 2 * d.npairs * d.Kp * 2;
+  d.b_bytes = (size_t)d.Np2 * 2 * d.npairs * d.Kp * 2;
+  d.e_bytes = ((size_t)d.Mp + d.Np2 / 2 + 64) * sizeof(int);
+  return d;
+}
+
+void upload_pairs(int nslices) {
+  static int loaded = -1;
+  if (loaded == nslices) return;
+  int si[MAX_PAIRS], sj[MAX_PAIRS], p = 0;
+  // by order o = i + j, then by i
+  for (int o = 0; o < nslices; ++o)
+    for (int i = 0; i <= o; ++i) {
+      si[p] = i;
+      sj[p] = o - i;
+      ++p;
+    }
+  CVS_CUDA(cudaMemcpyToSymbol(c_si, si, sizeof(int) * p));
+  CVS_CUDA(cudaMemcpyToSymbol(c_sj, sj, sizeof(int) * p));
+  loaded = nslices;
+}
+
+}  // namespace
+
+size_t slice_workspace_bytes(int M, int N, int K, int nslices) {
+  SDims d = sdims_of(M, N, K, nslices);
+  return d.a_bytes + d.b_bytes + d.e_bytes + 256;
+}
+
+void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
+                 double alpha, View A, View B, double beta, View C, void* work,
+                 size_t work_bytes, int* err) {
+  if (M <= 0 || N <= 0) return;
+  CVS_REQUIRE(nslices == 4 || nslices == 7, -1, "zgemm_slice: 4 or 7 slices");
+  SDims d = sdims_of(M, N, K, nslices);
+  CVS_REQUIRE(work_bytes >= d.a_bytes + d.b_bytes + d.e_bytes, -1,
+              "zgemm_slice: workspace too small");
+  static bool attr = false;
+  if (!attr) {
+    CVS_CUDA(cudaFuncSetAttribute(tc_slice_kernel,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  S_SMEM));
+    attr = true;
+  }
+  upload_pairs(nslices);
+  __nv_bfloat16* ap = (__nv_bfloat16*)work;
+  __nv_bfloat16* bp = (__nv_bfloat16*)((char*)work + d.a_bytes);
+  int* eA = (int*)((char*)work + d.a_bytes + d.b_bytes);
+  int* eB = eA + d.Mp;
+  row_exp_kernel<<<std::min(M, 152 * 16), 256, 0, s>>>(A, M, K, eA);
+  CVS_CHECK_LAUNCH();
+  col_exp_kernel<<<std::min(N, 152 * 16), 256, 0, s>>>(B, K, N, eB);
+  CVS_CHECK_LAUNCH();
+  const unsigned ga = grid1d((int64_t)d.Mp * d.Kp, 256);
+  const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * d.Kp, 256);
+  if (nslices == 4) {
+    slice_pack_a<4><<<ga, 256, 0, s>>>(A, M, K, d.Mp, d.Kp, d.npairs, eA, ap);
+    CVS_CHECK_LAUNCH();
+    slice_pack_b<4><<<gb, 256, 0, s>>>(B, K, N, d.Np2, d.Kp, d.npairs, eB, bp);
+  } else {
+    slice_pack_a<7><<<ga, 256, 0, s>>>(A, M, K, d.Mp, d.Kp, d.npairs, eA, ap);
+    CVS_CHECK_LAUNCH();
+    slice_pack_b<7><<<gb, 256, 0, s>>>(B, K, N, d.Np2, d.Kp, d.npairs, eB, bp);
+  }
+  CVS_CHECK_LAUNCH();
+  const int64_t kcols = (int64_t)2 * d.npairs * d.Kp;
+  CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
+  CUtensorMap mb = make_map(bp, d.Np2, kcols, SBN);
+  const int ktpp = 2 * d.Kp / BK;
+  dim3 grid(d.Np2 / SBN, d.Mp / BM);
+  tc_slice_kernel<<<grid, 576, S_SMEM, s>>>(ma, mb, d.npairs, ktpp, M, N, eA,
+                                            eB, alpha, beta, C, err);
+  CVS_CHECK_LAUNCH();
 }
 
 }  // namespace cvs

@@ -10,13 +10,23 @@ namespace cvs {
 void zgemm_f64(cudaStream_t s, int M, int N, int K, double alpha, View A,
                View B, double beta, View C, int batch = 1);
 
-// Same contract on the tcgen05 tensor cores: A and B are split into
-// bf16 hi/lo parts, three products per real product, FP32 accumulation.
-// `work` must hold tc_workspace_bytes(M, N, K) bytes.
-size_t tc_workspace_bytes(int M, int N, int K);
-void zgemm_tc(cudaStream_t s, int M, int N, int K, double alpha, View A,
-              View B, double beta, View C, void* work, size_t work_bytes);
+// Same contract on the tcgen05 tensor cores: A and B are split into bf16
+// parts, nprod = 3 (hi/lo, BF16x3) or 6 (hi/mid/lo, BF16x6) products per
+// real product, FP32 accumulation.  `work` must hold
+// tc_workspace_bytes(M, N, K, nprod) bytes; a bounded wait that expires
+// writes a non-zero code to *err (device int, never cleared here).
+size_t tc_workspace_bytes(int M, int N, int K, int nprod);
+void zgemm_tc(cudaStream_t s, int nprod, int M, int N, int K, double alpha,
+              View A, View B, double beta, View C, void* work,
+              size_t work_bytes, int* err);
 bool tc_available();
+// Exact-accumulation slice GEMM on the tensor cores (see gemm_tc.cu):
+// nslices = 4 (10 slice products, ~2^-28 of row max x column max) or 7
+// (28 products, FP64 class).
+size_t slice_workspace_bytes(int M, int N, int K, int nslices);
+void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
+                 double alpha, View A, View B, double beta, View C, void* work,
+                 size_t work_bytes, int* err);
 
 // C = beta * C over a view
 void scale_view(cudaStream_t s, int M, int N, double beta, View C, int batch);

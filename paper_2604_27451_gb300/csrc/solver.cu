@@ -152,11 +152,21 @@ struct cvsadc_ctx {
   // scratch
   DBuf s_big1, s_big2, s_S, s_R, s_Y, s_V, s_part, s_small, s_tc;
   DBuf dv_V, dv_W, dv_X, dv_AX, dv_T, dv_H, dv_A, dv_U, dv_w, dv_misc;
+  DBuf err;  // device int: non-zero after a bounded device wait expired
 
   void sync() { CVS_CUDA(cudaStreamSynchronize(stream)); }
 };
 
 namespace {
+
+bool valid_precision(int p) {
+  return p == CVSADC_FP64 || p == CVSADC_MIXED_BF16X3 ||
+         p == CVSADC_MIXED_SLICE4 || p == CVSADC_FP64_SLICE7;
+}
+// precisions whose results need the FP64 residual correction
+bool needs_refine(int p) {
+  return p == CVSADC_MIXED_BF16X3 || p == CVSADC_MIXED_SLICE4;
+}
 
 // --------------------------------------------------------------- GEMM hub
 void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
@@ -167,14 +177,15 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
   check_view(A, M, K, batch, "A");
   check_view(B, K, N, batch, "B");
   check_view(C, M, N, batch, "C");
-  if (prec == CVSADC_MIXED_BF16X3 && batch == 1 && tc_available()) {
-    size_t need = tc_workspace_bytes(M, N, K);
-    c->s_tc.ensure(need);
-    zgemm_tc(c->stream, M, N, K, alpha, A, B, beta, C, c->s_tc.p, need);
-    return;
-  }
-  if (prec == CVSADC_MIXED_BF16X3 && batch > 1 && tc_available()) {
-    size_t need = tc_workspace_bytes(M, N, K);
+  // the tensor-core path pays a packing pass per operand: keep it for
+  // contractions with enough work per packed element
+  const bool tc = prec != CVSADC_FP64 && M >= 64 && N >= 32 && K >= 64 &&
+                  (double)M * N * K >= 1e7;
+  if (tc) {
+    CVS_REQUIRE(tc_available(), CVSADC_EINVAL,
+                "tensor-core precisions need an sm_103 GPU with tcgen05");
+    const int ns = prec == CVSADC_MIXED_SLICE4 ? 4 : prec == CVSADC_FP64_SLICE7 ? 7 : 0;
+    size_t need = ns ? slice_workspace_bytes(M, N, K, ns) : tc_workspace_bytes(M, N, K, 3);
     c->s_tc.ensure(need);
     for (int z = 0; z < batch; ++z) {
       View a = A, b = B, cc = C;
@@ -184,7 +195,12 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
       if (a.ext >= 0) a.ext -= z * A.batch;
       if (b.ext >= 0) b.ext -= z * B.batch;
       if (cc.ext >= 0) cc.ext -= z * C.batch;
-      zgemm_tc(c->stream, M, N, K, alpha, a, b, beta, cc, c->s_tc.p, need);
+      if (ns)
+        zgemm_slice(c->stream, ns, M, N, K, alpha, a, b, beta, cc, c->s_tc.p,
+                    need, c->err.as<int>());
+      else
+        zgemm_tc(c->stream, 3, M, N, K, alpha, a, b, beta, cc, c->s_tc.p, need,
+                 c->err.as<int>());
     }
     return;
   }
@@ -558,8 +574,7 @@ void validate(const cvsadc_params* p) {
   CVS_REQUIRE(p != nullptr, CVSADC_EINVAL, "params is NULL");
   CVS_REQUIRE(p->ncore >= 1 && p->nval >= 1 && p->nvirt >= 2 && p->naux >= 1,
               CVSADC_EINVAL, "partition sizes must be ncore>=1, nval>=1, nvirt>=2, naux>=1");
-  CVS_REQUIRE(p->precision == CVSADC_FP64 || p->precision == CVSADC_MIXED_BF16X3,
-              CVSADC_EINVAL, "unknown precision");
+  CVS_REQUIRE(valid_precision(p->precision), CVSADC_EINVAL, "unknown precision");
   int64_t n = (int64_t)p->ncore + p->nval + p->nvirt;
   int64_t o = (int64_t)p->ncore + p->nval;
   CVS_REQUIRE(n <= 20000 && (int64_t)p->naux * n * n < (1LL << 40), CVSADC_EINVAL,
@@ -627,17 +642,26 @@ struct DavResult {
   double maxres = 0.0;
 };
 
+// Block Davidson for the lowest nroots eigenpairs of M (sigma in `prec`,
+// all subspace algebra in FP64).  Restarts keep the nkeep lowest Ritz
+// vectors (about a third of the subspace), which retains much of the
+// Krylov information of the stiff doubles-dominated roots.  With
+// stop_on_stagnation the iteration also ends when the largest residual has
+// not halved over 50 iterations (the noise floor of a mixed-precision
+// sigma).
 DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
                         int max_sub, double tol, const cplx* X0, int nx0,
-                        cplx* Xout, double* wout) {
+                        cplx* Xout, double* wout,
+                        bool stop_on_stagnation = false) {
   const int64_t N = c->N;
   const int k = nroots;
   const int msub = std::max(max_sub, 2 * k + 2);
+  const int nkeep = std::max(k, std::min(msub / 3, msub - 2 * k));
   DavResult res;
   c->dv_V.ensure((size_t)msub * N * sizeof(cplx));
   c->dv_W.ensure((size_t)msub * N * sizeof(cplx));
-  c->dv_X.ensure((size_t)k * N * sizeof(cplx));
-  c->dv_AX.ensure((size_t)k * N * sizeof(cplx));
+  c->dv_X.ensure((size_t)nkeep * N * sizeof(cplx));
+  c->dv_AX.ensure((size_t)nkeep * N * sizeof(cplx));
   c->dv_T.ensure((size_t)k * N * sizeof(cplx));
   c->dv_H.ensure((size_t)msub * msub * sizeof(cplx));
   c->dv_A.ensure((size_t)msub * msub * sizeof(cplx));
@@ -730,7 +754,7 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     orthonormalise_append(W, nguess);
   }
   int m_done = 0;  // vectors whose sigma is known
-  std::vector<double> theta(k), rn2(k);
+  std::vector<double> theta(k), rn2(k), hist;
   std::vector<cplx> hostbuf;
   for (int it = 0; it < max_iter; ++it) {
     // sigma for new vectors
@@ -779,19 +803,33 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
         todo.push_back(r);
     }
     if (todo.empty() || it == max_iter - 1) break;
-    // restart (thick, to the k Ritz vectors) if the new block does not fit
+    if (stop_on_stagnation) {
+      hist.push_back(res.maxres);
+      if (hist.size() > 50 && res.maxres > 0.5 * hist[hist.size() - 51]) break;
+    }
+    // thick restart to the nkeep lowest Ritz vectors when the block does
+    // not fit
     if (m + (int)todo.size() > msub) {
-      CVS_CUDA(cudaMemcpyAsync(V, c->dv_X.p, (size_t)k * N * sizeof(cplx),
+      const int nk = std::min(nkeep, m);
+      ts_combine(s, V, c->dv_U.c(), nullptr, nullptr, m, m, nk, N, c->dv_X.c());
+      ts_combine(s, nullptr, nullptr, W, c->dv_U.c(), m, m, nk, N, c->dv_AX.c());
+      CVS_CUDA(cudaMemcpyAsync(V, c->dv_X.p, (size_t)nk * N * sizeof(cplx),
                                cudaMemcpyDeviceToDevice, s));
-      CVS_CUDA(cudaMemcpyAsync(W, c->dv_AX.p, (size_t)k * N * sizeof(cplx),
+      CVS_CUDA(cudaMemcpyAsync(W, c->dv_AX.p, (size_t)nk * N * sizeof(cplx),
                                cudaMemcpyDeviceToDevice, s));
-      // H = diag(theta)
+      // H = diag(theta_0 .. theta_{nk-1})
+      std::vector<double> th(nk);
+      CVS_CUDA(cudaMemcpyAsync(th.data(), c->dv_w.d(), nk * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+      c->sync();
       std::vector<cplx> h((size_t)msub * msub, cmake(0, 0));
-      for (int r = 0; r < k; ++r) h[(size_t)r * msub + r] = cmake(theta[r], 0);
+      for (int r = 0; r < nk; ++r) h[(size_t)r * msub + r] = cmake(th[r], 0);
       CVS_CUDA(cudaMemcpyAsync(c->dv_H.p, h.data(), h.size() * sizeof(cplx),
                                cudaMemcpyHostToDevice, s));
-      m = k;
-      m_done = k;
+      c->sync();
+      // the k wanted Ritz pairs are rows 0..k-1 of the new basis again
+      m = nk;
+      m_done = nk;
     }
     // append corrections of the unconverged roots
     for (size_t q = 0; q < todo.size(); ++q)
@@ -810,6 +848,15 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
   return res;
 }
 
+// Residual at which the mixed-precision Davidson hands over to the FP64
+// correction: a few times the sigma noise of the tensor-core GEMMs
+// (BF16X3 ~1e-5 relative, SLICE4 ~1e-8, on |M x| of O(10-100) Eh).
+double mixed_tolerance(int prec) {
+  const char* e = getenv("CVSADC_MIXED_TOL");
+  if (e && *e) return atof(e);
+  return prec == CVSADC_MIXED_BF16X3 ? 3e-4 : 1e-6;
+}
+
 void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
                     void* X, double* osc, cvsadc_info* info) {
   CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
@@ -825,19 +872,25 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
   DBuf Xd;
   Xd.ensure((size_t)k * c->N * sizeof(cplx));
   std::vector<double> w(k);
-  DavResult r = davidson_impl(c, p->precision, k, max_iter, max_sub, tol,
-                              nullptr, 0, Xd.c(), w.data());
+  double tol_phase = tol;
+  if (needs_refine(p->precision) && !(p->flags & CVSADC_FLAG_NO_REFINE))
+    tol_phase = std::max(tol, mixed_tolerance(p->precision));
+  DavResult r = davidson_impl(c, p->precision, k, max_iter, max_sub, tol_phase,
+                              nullptr, 0, Xd.c(), w.data(),
+                              needs_refine(p->precision));
   double t1 = now_ms();
   double t_ref = 0;
-  if (p->precision != CVSADC_FP64 && !(p->flags & CVSADC_FLAG_NO_REFINE)) {
-    // FP64 residual correction: Davidson in FP64 started from the
-    // converged mixed-precision Ritz vectors
+  if (needs_refine(p->precision) && !(p->flags & CVSADC_FLAG_NO_REFINE)) {
+    // FP64 residual correction: from the converged mixed-precision Ritz
+    // vectors, sigma in FP64, Rayleigh-Ritz, and correction steps, each
+    // costing one FP64 sigma per unconverged root
     DBuf X0;
     X0.ensure((size_t)k * c->N * sizeof(cplx));
     CVS_CUDA(cudaMemcpyAsync(X0.p, Xd.p, (size_t)k * c->N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, c->stream));
-    DavResult r2 = davidson_impl(c, CVSADC_FP64, k, 20, max_sub, tol, X0.c(), k,
-                                 Xd.c(), w.data());
+    int sweeps = p->refine_sweeps > 0 ? p->refine_sweeps : 2;
+    DavResult r2 = davidson_impl(c, CVSADC_FP64, k, sweeps, max_sub, tol, X0.c(),
+                                 k, Xd.c(), w.data());
     r.iters += r2.iters;
     r.sigmas += r2.sigmas;
     r.converged = r2.converged;
@@ -890,11 +943,26 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
   if (r.converged < k) throw Error{CVSADC_ENOTCONV, "Davidson did not converge"};
 }
 
+void check_device_error(cvsadc_ctx* c) {
+  if (!c->err.p) return;
+  int e = 0;
+  CVS_CUDA(cudaMemcpyAsync(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream));
+  CVS_CUDA(cudaStreamSynchronize(c->stream));
+  if (e != 0) {
+    CVS_CUDA(cudaMemsetAsync(c->err.p, 0, sizeof(int), c->stream));
+    char b[128];
+    snprintf(b, sizeof b, "a bounded device wait expired (code %d)", e);
+    throw Error{CVSADC_ETIMEOUT, b};
+  }
+}
+
 template <typename F>
 int guarded(cvsadc_ctx* c, F&& f) {
   try {
     if (c) CVS_CUDA(cudaSetDevice(c->device));
     f();
+    if (c) check_device_error(c);
     if (c) c->last_error.clear();
     return CVSADC_OK;
   } catch (const Error& e) {
@@ -928,6 +996,8 @@ int cvsadc_create(cvsadc_ctx** ctx, int device, void* cuda_stream) {
   c->device = device;
   int rc = guarded(c, [&] {
     init_kernel_attributes();
+    c->err.ensure(256);
+    CVS_CUDA(cudaMemset(c->err.p, 0, 256));
     if (cuda_stream) {
       c->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -1034,8 +1104,7 @@ int cvsadc_sigma(cvsadc_ctx* c, int32_t precision, int32_t flags,
   if (!c || !x || !sigma || nvec < 0) return CVSADC_EINVAL;
   return guarded(c, [&] {
     CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
-    CVS_REQUIRE(precision == CVSADC_FP64 || precision == CVSADC_MIXED_BF16X3,
-                CVSADC_EINVAL, "unknown precision");
+    CVS_REQUIRE(valid_precision(precision), CVSADC_EINVAL, "unknown precision");
     if (nvec == 0) return;
     bool dev = flags & CVSADC_FLAG_DEVICE_PTRS;
     size_t bytes = (size_t)nvec * c->N * sizeof(cplx);
@@ -1051,6 +1120,46 @@ int cvsadc_sigma(cvsadc_ctx* c, int32_t precision, int32_t flags,
       CVS_CUDA(cudaMemcpyAsync(sigma, sd.p, bytes, cudaMemcpyDeviceToHost, c->stream));
       c->sync();
     }
+    c->sync();
+  });
+}
+
+int cvsadc_zgemm(cvsadc_ctx* c, int32_t precision, int32_t flags, int32_t M,
+                 int32_t N, int32_t K, const void* A, int64_t lda,
+                 const void* B, int64_t ldb, void* C, int64_t ldc) {
+  if (!c || !A || !B || !C || M < 0 || N < 0 || K < 0) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    CVS_REQUIRE(valid_precision(precision), CVSADC_EINVAL, "unknown precision");
+    CVS_REQUIRE(lda >= std::max(K, 1) && ldb >= std::max(N, 1) &&
+                    ldc >= std::max(N, 1),
+                CVSADC_EINVAL, "leading dimension too small");
+    if (M == 0 || N == 0) return;
+    bool dev = flags & CVSADC_FLAG_DEVICE_PTRS;
+    size_t ab = (size_t)M * lda * sizeof(cplx), bb = (size_t)K * ldb * sizeof(cplx),
+           cb = (size_t)M * ldc * sizeof(cplx);
+    DBuf da, db, dc;
+    const void *pa = A, *pb = B;
+    void* pc = C;
+    std::unique_ptr<RegGuard> ga, gb, gc;
+    if (dev) {
+      ga.reset(new RegGuard(A, ab));
+      gb.reset(new RegGuard(B, bb));
+      gc.reset(new RegGuard(C, cb));
+    } else {
+      upload(c, da, A, ab, false);
+      upload(c, db, B, bb, false);
+      dc.ensure(cb);
+      pa = da.p;
+      pb = db.p;
+      pc = dc.p;
+    }
+    if (K == 0) {
+      CVS_CUDA(cudaMemsetAsync(pc, 0, cb, c->stream));
+    } else {
+      gemm(c, precision, M, N, K, 1.0, view(pa, lda, 1), view(pb, ldb, 1), 0.0,
+           view(pc, ldc, 1));
+    }
+    if (!dev) download(c, C, dc.p, cb, false);
     c->sync();
   });
 }
