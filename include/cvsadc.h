@@ -116,6 +116,7 @@ typedef struct {
   double t_davidson_ms;    /* Davidson iterations */
   double t_refine_ms;      /* FP64 residual correction */
   double t_total_ms;
+  double t_sigma_ms;       /* device time of the sigma builds (CUDA events) */
 } cvsadc_info;
 
 typedef struct cvsadc_ctx cvsadc_ctx;
@@ -208,6 +209,21 @@ int cvsadc_sigma(cvsadc_ctx* ctx, int32_t precision, int32_t flags,
 int cvsadc_zgemm(cvsadc_ctx* ctx, int32_t precision, int32_t flags,
                  int32_t M, int32_t N, int32_t K, const void* A, int64_t lda,
                  const void* B, int64_t ldb, void* C, int64_t ldc);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts); a counter for launch accounting, never reset. */
+int64_t cvsadc_launch_count(void);
+
+/* Kernel timing for measurement: when enabled, every launch of the main
+ * GEMM kernels is bracketed by CUDA events on its stream.  kernel: 0 =
+ * tcgen05 BF16X3 GEMM, 1 = tcgen05 exact-slice GEMM, 2 = FP64 FMA GEMM.
+ * cvsadc_kernel_stats returns the launches, summed device milliseconds and
+ * summed algorithmic flops (8 M N K per complex GEMM) recorded since the
+ * last reset (synchronising the recorded events).  Process-wide. */
+void cvsadc_kernel_timing(int32_t enable);
+int cvsadc_kernel_stats(int32_t kernel, int64_t* launches, double* ms,
+                        double* flops);
+void cvsadc_kernel_stats_reset(void);
 
 /* Davidson on the prepared problem (see cvsadc_solve for outputs). */
 int cvsadc_davidson(cvsadc_ctx* ctx, const cvsadc_params* params,

@@ -50,6 +50,7 @@ class Info(ctypes.Structure):
         ("emp2", ctypes.c_double), ("max_residual", ctypes.c_double),
         ("t_prepare_ms", ctypes.c_double), ("t_davidson_ms", ctypes.c_double),
         ("t_refine_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
+        ("t_sigma_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -77,6 +78,12 @@ _SIGNATURES = {
                                     ctypes.c_int32]),
     "cvsadc_davidson": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp,
                                        ctypes.POINTER(Info)]),
+    "cvsadc_launch_count": (ctypes.c_int64, []),
+    "cvsadc_kernel_timing": (None, [ctypes.c_int32]),
+    "cvsadc_kernel_stats": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double)]),
+    "cvsadc_kernel_stats_reset": (None, []),
     "cvsadc_zgemm": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64,
                                     _vp, ctypes.c_int64, _vp, ctypes.c_int64]),

@@ -33,7 +33,14 @@ struct Error {
     }                                                                         \
   } while (0)
 
-#define CVS_CHECK_LAUNCH() CVS_CUDA(cudaGetLastError())
+// every kernel launch of the library goes through CVS_CHECK_LAUNCH, which
+// also counts it
+extern unsigned long long g_launch_count;
+#define CVS_CHECK_LAUNCH()                                 \
+  do {                                                     \
+    __atomic_fetch_add(&::cvs::g_launch_count, 1ull, __ATOMIC_RELAXED); \
+    CVS_CUDA(cudaGetLastError());                          \
+  } while (0)
 
 #define CVS_REQUIRE(cond, code, text)                                         \
   do {                                                                        \
@@ -170,6 +177,19 @@ __device__ __forceinline__ int64_t vcol(const View& v, int64_t c) {
   int64_t h = c / v.c_lo;
   return h * v.cs_hi + (c - h * v.c_lo) * v.cs_lo;
 }
+
+// ------------------------------------------------------ kernel timing
+// When enabled, the GEMM drivers bracket each launch of their main kernel
+// with CUDA events on the launching stream and record its algorithmic
+// flops; kstats_collect() turns finished pairs into per-kernel totals.
+enum KernelId { K_TC_BF16X3 = 0, K_TC_SLICE = 1, K_F64_GEMM = 2, K_NKERNELS = 3 };
+bool kstats_enabled();
+void kstats_set(bool on);
+// returns an opaque token to pass to kstats_end (or -1 when disabled)
+int kstats_begin(cudaStream_t s, int kernel, double flops);
+void kstats_end(cudaStream_t s, int token);
+void kstats_collect(int kernel, int64_t* count, double* ms, double* flops);
+void kstats_reset();
 
 // ------------------------------------------------------------- launching
 static inline unsigned grid1d(int64_t n, int block, int64_t cap = 152 * 32) {

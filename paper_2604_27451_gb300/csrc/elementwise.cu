@@ -5,6 +5,8 @@
 #include "kernels.cuh"
 
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 namespace cvs {
 
@@ -565,14 +567,81 @@ __global__ void phase_apply_kernel(cplx* x, int64_t N, const double* pv,
 }
 
 
-// A[i][j] = (H[i][j] + conj(H[j][i])) / 2, H with leading dimension ldh
-__global__ void hermitize_kernel(const cplx* H, int ldh, int m, cplx* A) {
+// A[i][j] = (h(i,j) + conj(h(j,i))) / 2 where h(i,j) = H[i][j] if that
+// entry was computed (column j >= jdone, or row i < jdone), else
+// conj(H[j][i]); H has leading dimension ldh
+__global__ void hermitize_kernel(const cplx* H, int ldh, int m, int jdone,
+                                 cplx* A) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
        e < (int64_t)m * m; e += (int64_t)gridDim.x * blockDim.x) {
     int i = e / m, j = e % m;
-    cplx a = H[(int64_t)i * ldh + j], b = H[(int64_t)j * ldh + i];
+    bool vij = (j >= jdone) || (i < jdone);
+    bool vji = (i >= jdone) || (j < jdone);
+    cplx hij = H[(int64_t)i * ldh + j], hji = H[(int64_t)j * ldh + i];
+    cplx a = vij ? hij : cconj(hji);
+    cplx b = vji ? hji : cconj(hij);
     A[e] = cmake(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
   }
+}
+
+// Orthonormalising transform of a block of cnt vectors from their Gram
+// matrix G (cnt x cnt, leading dimension ldg): Gram-Schmidt in coefficient
+// space with the G inner product, two projection passes per column; a
+// column is dropped when its remaining norm is below tol * norm0[j].
+// X[j][q] (leading dimension cnt) holds kept column q; *kept = their count.
+__global__ void block_orth_kernel(const cplx* G, int ldg, int cnt,
+                                  const double* norm0, double tol, cplx* X,
+                                  int* kept) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int nk = 0;
+  cplx u[64], gu[64];
+  for (int j = 0; j < cnt; ++j) {
+    for (int a = 0; a < cnt; ++a) u[a] = cmake(a == j ? 1.0 : 0.0, 0.0);
+    for (int pass = 0; pass < 2; ++pass) {
+      // gu = G u
+      for (int a = 0; a < cnt; ++a) {
+        cplx acc = cmake(0, 0);
+        for (int b = 0; b < cnt; ++b) acc = cadd(acc, cmul(G[a * ldg + b], u[b]));
+        gu[a] = acc;
+      }
+      for (int q = 0; q < nk; ++q) {
+        // c = x_q^H G u
+        cplx c = cmake(0, 0);
+        for (int a = 0; a < cnt; ++a) c = cadd(c, cdotc(X[a * cnt + q], gu[a]));
+        for (int a = 0; a < cnt; ++a) u[a] = csub(u[a], cmul(c, X[a * cnt + q]));
+      }
+    }
+    for (int a = 0; a < cnt; ++a) {
+      cplx acc = cmake(0, 0);
+      for (int b = 0; b < cnt; ++b) acc = cadd(acc, cmul(G[a * ldg + b], u[b]));
+      gu[a] = acc;
+    }
+    double nrm2 = 0;
+    for (int a = 0; a < cnt; ++a) nrm2 += cdotc(u[a], gu[a]).x;
+    double nrm = sqrt(fmax(nrm2, 0.0));
+    if (nrm > tol * norm0[j] && nrm > 1e-300) {
+      for (int a = 0; a < cnt; ++a) X[a * cnt + nk] = cscale(u[a], 1.0 / nrm);
+      ++nk;
+    }
+  }
+  *kept = nk;
+}
+
+// H[i][j] = conj(H[j][i]) for i in [i0, i1), j < i0 (the block of new rows
+// against old columns, known from Hermiticity once the new columns exist)
+__global__ void herm_fill_kernel(cplx* H, int ldh, int i0, int i1) {
+  const int64_t total = (int64_t)(i1 - i0) * i0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = i0 + (int)(e / i0), j = (int)(e % i0);
+    H[(int64_t)i * ldh + j] = cconj(H[(int64_t)j * ldh + i]);
+  }
+}
+
+__global__ void gram_diag_sqrt_kernel(const cplx* G, int ldg, int cnt,
+                                      double* out) {
+  int j = threadIdx.x;
+  if (j < cnt) out[j] = sqrt(fmax(G[j * ldg + j].x, 0.0));
 }
 
 // X[r][c] *= s[r]
@@ -773,8 +842,30 @@ void init_kernel_attributes() {
 }
 
 
-void hermitize(cudaStream_t s, const cplx* H, int ldh, int m, cplx* A) {
-  hermitize_kernel<<<grid1d((int64_t)m * m, 256), 256, 0, s>>>(H, ldh, m, A);
+void hermitize(cudaStream_t s, const cplx* H, int ldh, int m, cplx* A,
+               int jdone) {
+  hermitize_kernel<<<grid1d((int64_t)m * m, 256), 256, 0, s>>>(H, ldh, m,
+                                                               jdone, A);
+  CVS_CHECK_LAUNCH();
+}
+
+void herm_fill(cudaStream_t s, cplx* H, int ldh, int i0, int i1) {
+  if (i0 <= 0 || i1 <= i0) return;
+  herm_fill_kernel<<<grid1d((int64_t)(i1 - i0) * i0, 256), 256, 0, s>>>(H, ldh,
+                                                                       i0, i1);
+  CVS_CHECK_LAUNCH();
+}
+
+void block_orth(cudaStream_t s, const cplx* G, int ldg, int cnt,
+                const double* norm0, double tol, cplx* X, int* kept) {
+  CVS_REQUIRE(cnt >= 1 && cnt <= 64, -1, "block_orth: at most 64 vectors");
+  block_orth_kernel<<<1, 32, 0, s>>>(G, ldg, cnt, norm0, tol, X, kept);
+  CVS_CHECK_LAUNCH();
+}
+
+void gram_diag_sqrt(cudaStream_t s, const cplx* G, int ldg, int cnt,
+                    double* out) {
+  gram_diag_sqrt_kernel<<<1, 64, 0, s>>>(G, ldg, cnt, out);
   CVS_CHECK_LAUNCH();
 }
 
@@ -783,6 +874,75 @@ void scale_rows(cudaStream_t s, cplx* X, int rows, int cols, int ld,
   scale_rows_kernel<<<grid1d((int64_t)rows * cols, 256), 256, 0, s>>>(
       X, rows, cols, ld, sc);
   CVS_CHECK_LAUNCH();
+}
+
+
+// ------------------------------------------------------ kernel timing
+namespace {
+struct KPair {
+  cudaEvent_t a, b;
+  int kernel;
+  double flops;
+};
+std::mutex g_ks_mu;
+std::vector<KPair> g_ks_pending;
+bool g_ks_on = false;
+int64_t g_ks_count[K_NKERNELS];
+double g_ks_ms[K_NKERNELS], g_ks_flops[K_NKERNELS];
+}  // namespace
+
+bool kstats_enabled() { return g_ks_on; }
+void kstats_set(bool on) { g_ks_on = on; }
+
+int kstats_begin(cudaStream_t s, int kernel, double flops) {
+  if (!g_ks_on) return -1;
+  std::lock_guard<std::mutex> l(g_ks_mu);
+  KPair p;
+  CVS_CUDA(cudaEventCreate(&p.a));
+  CVS_CUDA(cudaEventCreate(&p.b));
+  p.kernel = kernel;
+  p.flops = flops;
+  CVS_CUDA(cudaEventRecord(p.a, s));
+  g_ks_pending.push_back(p);
+  return (int)g_ks_pending.size() - 1;
+}
+
+void kstats_end(cudaStream_t s, int token) {
+  if (token < 0) return;
+  std::lock_guard<std::mutex> l(g_ks_mu);
+  CVS_CUDA(cudaEventRecord(g_ks_pending[token].b, s));
+}
+
+static void kstats_drain() {
+  for (auto& p : g_ks_pending) {
+    CVS_CUDA(cudaEventSynchronize(p.b));
+    float ms = 0;
+    CVS_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+    g_ks_count[p.kernel] += 1;
+    g_ks_ms[p.kernel] += ms;
+    g_ks_flops[p.kernel] += p.flops;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_ks_pending.clear();
+}
+
+void kstats_collect(int kernel, int64_t* count, double* ms, double* flops) {
+  std::lock_guard<std::mutex> l(g_ks_mu);
+  kstats_drain();
+  *count = g_ks_count[kernel];
+  *ms = g_ks_ms[kernel];
+  *flops = g_ks_flops[kernel];
+}
+
+void kstats_reset() {
+  std::lock_guard<std::mutex> l(g_ks_mu);
+  kstats_drain();
+  for (int k = 0; k < K_NKERNELS; ++k) {
+    g_ks_count[k] = 0;
+    g_ks_ms[k] = 0;
+    g_ks_flops[k] = 0;
+  }
 }
 
 }  // namespace cvs

@@ -1,11 +1,21 @@
 // Complex FP64 GEMM on the CUDA cores (FP64 FMA), C = alpha*A*B + beta*C,
 // for matrices given as two-mode strided views (common.cuh).  This is the
 // arithmetic of the FP64 path: every contraction of t2, M11 and the sigma
-// vector goes through it when precision = CVSADC_FP64.
+// vector goes through it when precision = CVSADC_FP64, and the small
+// contractions of every precision do.
 //
-// Tile 64x64x8, 256 threads, 4x4 complex outputs per thread, register
-// prefetch of the next K tile.  Loads are mapped so that consecutive
-// threads follow whichever mode of the operand has unit stride.
+// Tile kernel: 64x64x8 tiles, 256 threads, 4x4 complex outputs per thread,
+// register prefetch of the next K tile; loads follow whichever mode of the
+// operand has unit stride.  Outputs with few tiles and a long K are split
+// along K (each z-slice writes alpha * partial product to a dense buffer,
+// a reduction adds them and beta * C).
+//
+// Small-output kernel: for M*N <= 4096 and a long K (e.g. the ncore x ncore
+// and ncore x nvirt intermediates, K up to 10^6-10^7) every block takes a K
+// chunk, stages A and B slices in shared memory and accumulates all M*N
+// dot products; the partials are reduced the same way.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -20,20 +30,32 @@ __device__ __forceinline__ cplx ldv(const cplx* p, int conj) {
   return v;
 }
 
+// part == nullptr: z is the batch index (operand batch strides), full K.
+// part != nullptr: z is a K slice [z*kchunk, (z+1)*kchunk); alpha * the
+// partial product goes to part[z][M][N].
 __global__ void __launch_bounds__(256)
     zgemm_f64_kernel(int M, int N, int K, double alpha, View A, View B,
-                     double beta, View C, int a_kfast, int b_kfast) {
+                     double beta, View C, int a_kfast, int b_kfast,
+                     int kchunk, cplx* part) {
   __shared__ cplx As[BK][BM];
   __shared__ cplx Bs[BK][BN];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int64_t z = blockIdx.z;
-  const cplx* Ap = A.p + z * A.batch;
-  const cplx* Bp = B.p + z * B.batch;
-  cplx* Cp = C.p + z * C.batch;
+  const cplx* Ap = A.p;
+  const cplx* Bp = B.p;
+  cplx* Cp = C.p;
+  int kb = 0, ke = K;
+  if (part) {
+    kb = (int)(z * kchunk);
+    ke = min(K, kb + kchunk);
+  } else {
+    Ap += z * A.batch;
+    Bp += z * B.batch;
+    Cp += z * C.batch;
+  }
 
-  // load assignment: 2 elements of each tile per thread
   int am[2], ak[2], bk[2], bn[2];
   int64_t aro[2], bco[2];
   bool aok[2], bok[2];
@@ -65,11 +87,11 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       int ka = k0 + ak[e];
-      ra[e] = (aok[e] && ka < K) ? ldv(Ap + aro[e] + vcol(A, ka), A.conj)
-                                 : cmake(0, 0);
-      int kb = k0 + bk[e];
-      rb[e] = (bok[e] && kb < K) ? ldv(Bp + vrow(B, kb) + bco[e], B.conj)
-                                 : cmake(0, 0);
+      ra[e] = (aok[e] && ka < ke) ? ldv(Ap + aro[e] + vcol(A, ka), A.conj)
+                                  : cmake(0, 0);
+      int kb2 = k0 + bk[e];
+      rb[e] = (bok[e] && kb2 < ke) ? ldv(Bp + vrow(B, kb2) + bco[e], B.conj)
+                                   : cmake(0, 0);
     }
   };
   auto store = [&]() {
@@ -86,12 +108,14 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.0;
 
-  const int ntiles = (K + BK - 1) / BK;
-  load(0);
-  store();
+  const int ntiles = (ke - kb + BK - 1) / BK;
+  if (ntiles > 0) {
+    load(kb);
+    store();
+  }
   __syncthreads();
   for (int t = 0; t < ntiles; ++t) {
-    if (t + 1 < ntiles) load((t + 1) * BK);
+    if (t + 1 < ntiles) load(kb + (t + 1) * BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       cplx a[4], b[4];
@@ -120,13 +144,17 @@ __global__ void __launch_bounds__(256)
   for (int i = 0; i < 4; ++i) {
     int r = m0 + ty + 16 * i;
     if (r >= M) continue;
-    int64_t ro = vrow(C, r);
+    int64_t ro = part ? 0 : vrow(C, r);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int c = n0 + tx + 16 * j;
       if (c >= N) continue;
-      cplx* dst = Cp + ro + vcol(C, c);
       cplx v = cmake(alpha * accr[i][j], alpha * acci[i][j]);
+      if (part) {
+        part[(z * M + r) * (int64_t)N + c] = v;
+        continue;
+      }
+      cplx* dst = Cp + ro + vcol(C, c);
       if (beta != 0.0) {
         cplx o = *dst;
         v.x += beta * o.x;
@@ -136,22 +164,163 @@ __global__ void __launch_bounds__(256)
     }
   }
 }
+
+// all M*N (<= 4096) dot products over a K chunk per block
+constexpr int STK = 16;
+__global__ void __launch_bounds__(256)
+    zgemm_smallmn_kernel(int M, int N, int K, double alpha, View A, View B,
+                         int kchunk, cplx* part) {
+  extern __shared__ cplx sh[];
+  cplx* sa = sh;            // [M][STK]
+  cplx* sb = sh + M * STK;  // [N][STK]
+  const int npairs = M * N;
+  const int per = (npairs + blockDim.x - 1) / blockDim.x;  // <= 16
+  double ar[16], ai[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) ar[q] = ai[q] = 0.0;
+  const int kb = blockIdx.x * kchunk, ke = min(K, kb + kchunk);
+  for (int k0 = kb; k0 < ke; k0 += STK) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < (M + N) * STK; e += blockDim.x) {
+      int row = e / STK, kk = e % STK, k = k0 + kk;
+      cplx v = cmake(0, 0);
+      if (k < ke) {
+        if (row < M) {
+          v = A.p[vrow(A, row) + vcol(A, k)];
+          if (A.conj) v.y = -v.y;
+        } else {
+          v = B.p[vrow(B, k) + vcol(B, row - M)];
+          if (B.conj) v.y = -v.y;
+        }
+      }
+      sh[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      if (q >= per) break;
+      int pr = threadIdx.x + q * blockDim.x;
+      if (pr >= npairs) break;
+      const cplx* x = sa + (pr / N) * STK;
+      const cplx* y = sb + (pr % N) * STK;
+      double sr = 0, si = 0;
+#pragma unroll
+      for (int kk = 0; kk < STK; ++kk) {
+        sr = fma(x[kk].x, y[kk].x, sr);
+        sr = fma(-x[kk].y, y[kk].y, sr);
+        si = fma(x[kk].x, y[kk].y, si);
+        si = fma(x[kk].y, y[kk].x, si);
+      }
+      ar[q] += sr;
+      ai[q] += si;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    if (q >= per) break;
+    int pr = threadIdx.x + q * blockDim.x;
+    if (pr >= npairs) break;
+    part[(int64_t)blockIdx.x * npairs + pr] = cmake(alpha * ar[q], alpha * ai[q]);
+  }
+}
+
+// C(m, n) = sum_z part[z][m][n] + beta * C(m, n)
+__global__ void splitk_reduce_kernel(int M, int N, int nz, const cplx* part,
+                                     double beta, View C) {
+  const int64_t MN = (int64_t)M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < MN;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    double sr = 0, si = 0;
+    for (int z = 0; z < nz; ++z) {
+      cplx v = part[z * MN + idx];
+      sr += v.x;
+      si += v.y;
+    }
+    int r = idx / N, c = idx % N;
+    cplx* d = C.p + vrow(C, r) + vcol(C, c);
+    if (beta != 0.0) {
+      cplx o = *d;
+      sr += beta * o.x;
+      si += beta * o.y;
+    }
+    *d = cmake(sr, si);
+  }
+}
 }  // namespace
 
+void splitk_reduce(cudaStream_t s, int M, int N, int nz, const cplx* part,
+                   double beta, View C) {
+  splitk_reduce_kernel<<<grid1d((int64_t)M * N, 256), 256, 0, s>>>(M, N, nz,
+                                                                   part, beta, C);
+  CVS_CHECK_LAUNCH();
+}
+
+int f64_splits(int M, int N, int K) {
+  const int64_t tiles = (int64_t)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  if (tiles >= 2 * 152 || K < 4096) return 1;
+  int64_t s = (4 * 152 + tiles - 1) / tiles;
+  s = std::min<int64_t>(s, K / 2048);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(s, 1024));
+}
+
+bool smallmn_ok(int M, int N, int K) {
+  return (int64_t)M * N <= 4096 && M + N <= 384 && K >= 4096;
+}
+int smallmn_blocks(int M, int N, int K) {
+  (void)M;
+  (void)N;
+  int64_t b = std::min<int64_t>(4 * 152, (K + 1023) / 1024);
+  return (int)std::max<int64_t>(1, b);
+}
+
 void zgemm_f64(cudaStream_t s, int M, int N, int K, double alpha, View A,
-               View B, double beta, View C, int batch) {
+               View B, double beta, View C, int batch, cplx* part,
+               size_t part_elems) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   if (K <= 0) {
     // C = beta * C
     scale_view(s, M, N, beta, C, batch);
     return;
   }
+  if (batch == 1 && part && smallmn_ok(M, N, K)) {
+    const int nb = smallmn_blocks(M, N, K);
+    if ((size_t)nb * M * N <= part_elems) {
+      const int kchunk = (K + nb - 1) / nb;
+      size_t sh = (size_t)(M + N) * STK * sizeof(cplx);
+      zgemm_smallmn_kernel<<<nb, 256, sh, s>>>(M, N, K, alpha, A, B, kchunk,
+                                               part);
+      CVS_CHECK_LAUNCH();
+      splitk_reduce(s, M, N, nb, part, beta, C);
+      return;
+    }
+  }
   int a_kfast = (A.cs_lo == 1) ? 1 : 0;
   int b_kfast = (B.rs_lo == 1) ? 1 : 0;
+  const int sp = (batch == 1 && part) ? f64_splits(M, N, K) : 1;
+  if (sp > 1 && (size_t)sp * M * N <= part_elems) {
+    const int kchunk = ((K + sp - 1) / sp + BK - 1) / BK * BK;
+    const int nz = (K + kchunk - 1) / kchunk;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nz);
+    const int tok = kstats_begin(s, K_F64_GEMM, 8.0 * M * N * (double)K);
+    zgemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, B, beta, C,
+                                          a_kfast, b_kfast, kchunk, part);
+    CVS_CHECK_LAUNCH();
+    kstats_end(s, tok);
+    splitk_reduce(s, M, N, nz, part, beta, C);
+    return;
+  }
   dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-  zgemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, B, beta, C,
-                                        a_kfast, b_kfast);
+  const int tok = kstats_begin(s, K_F64_GEMM, 8.0 * M * N * (double)K * batch);
+  zgemm_f64_kernel<<<grid, 256, 0, s>>>(M, N, K, alpha, A, B, beta, C, a_kfast,
+                                        b_kfast, 0, nullptr);
   CVS_CHECK_LAUNCH();
+  kstats_end(s, tok);
+}
+
+void init_gemm_attributes() {
+  CVS_CUDA(cudaFuncSetAttribute(zgemm_smallmn_kernel,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (384 * STK) * (int)sizeof(cplx)));
 }
 
 }  // namespace cvs

@@ -168,8 +168,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
-                   const __grid_constant__ CUtensorMap tmB, int nkt, int M,
-                   int N, double alpha, double beta, View C, int* err) {
+                   const __grid_constant__ CUtensorMap tmB, int nkt, int zkt,
+                   int M, int N, double alpha, double beta, View C,
+                   cplx* part, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -182,6 +183,8 @@ __global__ void __launch_bounds__(128, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int z = blockIdx.z;
+  const int ktb = z * zkt, kte = min(nkt, ktb + zkt);  // non-empty by launch
 
   if (threadIdx.x == 0) {
     fail = 0;
@@ -207,10 +210,11 @@ __global__ void __launch_bounds__(128, 1)
 
   if (threadIdx.x == 0) {
     // TMA producer
-    for (int kt = 0; kt < nkt; ++kt) {
-      const int s = kt % STAGES;
-      const uint32_t ph = (kt / STAGES) & 1;
-      if (kt >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+    for (int i = 0; i < kte - ktb; ++i) {
+      const int kt = ktb + i;
+      const int s = i % STAGES;
+      const uint32_t ph = (i / STAGES) & 1;
+      if (i >= STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
         fail = 1;
         break;
       }
@@ -222,10 +226,9 @@ __global__ void __launch_bounds__(128, 1)
   } else if (threadIdx.x == 32) {
     // MMA issuer
     const uint32_t id = idesc_bf16(BM, BN);
-    int kt = 0;
-    for (; kt < nkt; ++kt) {
-      const int s = kt % STAGES;
-      const uint32_t ph = (kt / STAGES) & 1;
+    for (int i = 0; i < kte - ktb; ++i) {
+      const int s = i % STAGES;
+      const uint32_t ph = (i / STAGES) & 1;
       if (!mbar_wait(&full[s], ph)) {
         fail = 2;
         break;
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(128, 1)
       const uint64_t bd = sdesc(smem_u32(sB + s * B_TILE));
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk)
-        umma(tmem, ad + 2 * kk, bd + 2 * kk, id, (kt | kk) ? 1u : 0u);
+        umma(tmem, ad + 2 * kk, bd + 2 * kk, id, (i | kk) ? 1u : 0u);
       umma_commit(&empty[s]);
     }
     umma_commit(done);
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(128, 1)
   fence_after();
   if (ok && !fail) {
     const int m = m0 + warp * 32 + lane;
-    const int64_t ro = m < M ? vrow(C, m) : 0;
+    const int64_t ro = (m < M && !part) ? vrow(C, m) : 0;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 16) {
       float v[16];
@@ -256,8 +259,12 @@ __global__ void __launch_bounds__(128, 1)
         for (int q = 0; q < 8; ++q) {
           const int n = (n0 + c) / 2 + q;
           if (n < N) {
-            cplx* d = C.p + ro + vcol(C, n);
             cplx o = cmake(alpha * (double)v[2 * q], alpha * (double)v[2 * q + 1]);
+            if (part) {
+              part[((int64_t)z * M + m) * N + n] = o;
+              continue;
+            }
+            cplx* d = C.p + ro + vcol(C, n);
             if (beta != 0.0) {
               cplx old = *d;
               o.x += beta * old.x;
@@ -293,7 +300,7 @@ __device__ __forceinline__ void split(double x, __nv_bfloat16* p) {
 
 // A' [Mp][2 NP Kp]: row m, segment 2p + {0: re, 1: im} of part pa(p)
 template <int NP>
-__global__ void pack_a_kernel(View A, int M, int K, int Mp, int Kp,
+__global__ void pack_a_kernel(View A, int M, int K, int k0, int Mp, int Kp,
                               __nv_bfloat16* out) {
   constexpr int PARTS = Split<NP>::parts;
   const int64_t ld = (int64_t)2 * NP * Kp;
@@ -303,7 +310,7 @@ __global__ void pack_a_kernel(View A, int M, int K, int Mp, int Kp,
     const int m = idx / Kp, k = idx % Kp;
     cplx a = cmake(0, 0);
     if (m < M && k < K) {
-      a = A.p[vrow(A, m) + vcol(A, k)];
+      a = A.p[vrow(A, m) + vcol(A, k0 + k)];
       if (A.conj) a.y = -a.y;
     }
     __nv_bfloat16 re[PARTS], im[PARTS];
@@ -320,7 +327,7 @@ __global__ void pack_a_kernel(View A, int M, int K, int Mp, int Kp,
 
 // B' [Np2][2 NP Kp]: rows 2n (real part column) and 2n+1 (imaginary)
 template <int NP>
-__global__ void pack_b_kernel(View B, int K, int N, int Np2, int Kp,
+__global__ void pack_b_kernel(View B, int K, int k0, int N, int Np2, int Kp,
                               __nv_bfloat16* out) {
   constexpr int PARTS = Split<NP>::parts;
   const int64_t ld = (int64_t)2 * NP * Kp;
@@ -330,7 +337,7 @@ __global__ void pack_b_kernel(View B, int K, int N, int Np2, int Kp,
     const int n = idx / Kp, k = idx % Kp;
     cplx b = cmake(0, 0);
     if (n < N && k < K) {
-      b = B.p[vrow(B, k) + vcol(B, n)];
+      b = B.p[vrow(B, k0 + k) + vcol(B, n)];
       if (B.conj) b.y = -b.y;
     }
     __nv_bfloat16 re[PARTS], im[PARTS];
@@ -427,43 +434,76 @@ bool tc_available() {
   return avail == 1;
 }
 
+// packed-operand budget per K chunk
+constexpr size_t PACK_BUDGET = (size_t)3 << 30;
+
+int chunk_k(int Mp, int Np2, int K, int nseg) {
+  // complex K per chunk so that both packed operands fit the budget
+  const size_t per_k = (size_t)(Mp + Np2) * nseg * 2;
+  int64_t kc = (int64_t)(PACK_BUDGET / per_k) / BK * BK;
+  kc = std::max<int64_t>(kc, BK);
+  return (int)std::min<int64_t>(kc, ((int64_t)K + BK - 1) / BK * BK);
+}
+
 size_t tc_workspace_bytes(int M, int N, int K, int nprod) {
   Dims d = dims_of(M, N, K, nprod);
-  return d.a_bytes + d.b_bytes + 256;
+  const int kc = chunk_k(d.Mp, d.Np2, K, d.nseg);
+  return (size_t)(d.Mp + d.Np2) * d.nseg * kc * 2 + 256;
+}
+
+// number of K splits for an output of `tiles` CTA tiles over `kt` k-tiles
+int tc_splits(int64_t tiles, int kt, int min_kt) {
+  if (tiles >= 152) return 1;
+  int64_t s = (2 * 152 + tiles - 1) / tiles;
+  s = std::min<int64_t>(s, std::max(1, kt / min_kt));
+  return (int)std::max<int64_t>(1, s);
 }
 
 void zgemm_tc(cudaStream_t s, int nprod, int M, int N, int K, double alpha,
               View A, View B, double beta, View C, void* work,
-              size_t work_bytes, int* err) {
+              size_t work_bytes, cplx* part, size_t part_elems, int* err) {
   if (M <= 0 || N <= 0) return;
   CVS_REQUIRE(nprod == 3 || nprod == 6, -1, "zgemm_tc: nprod must be 3 or 6");
   Dims d = dims_of(M, N, K, nprod);
-  CVS_REQUIRE(work_bytes >= d.a_bytes + d.b_bytes + 256, -1,
+  const int kc = chunk_k(d.Mp, d.Np2, K, d.nseg);
+  CVS_REQUIRE(work_bytes >= (size_t)(d.Mp + d.Np2) * d.nseg * kc * 2, -1,
               "zgemm_tc: workspace too small");
-  CVS_REQUIRE(d.Kp > 0, -1, "zgemm_tc: K must be positive");
   __nv_bfloat16* ap = (__nv_bfloat16*)work;
-  __nv_bfloat16* bp = (__nv_bfloat16*)((char*)work + d.a_bytes);
-  const unsigned ga = grid1d((int64_t)d.Mp * d.Kp, 256);
-  const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * d.Kp, 256);
-  if (nprod == 3) {
-    pack_a_kernel<3><<<ga, 256, 0, s>>>(A, M, K, d.Mp, d.Kp, ap);
+  __nv_bfloat16* bp = ap + (size_t)d.Mp * d.nseg * kc;
+  const int64_t tiles = (int64_t)(d.Np2 / BN) * (d.Mp / BM);
+  for (int k0 = 0; k0 < K; k0 += kc) {
+    const int Kc = std::min(kc, K - k0);
+    const int Kp = (Kc + BK - 1) / BK * BK;
+    const unsigned ga = grid1d((int64_t)d.Mp * Kp, 256);
+    const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * Kp, 256);
+    if (nprod == 3) {
+      pack_a_kernel<3><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, ap);
+      CVS_CHECK_LAUNCH();
+      pack_b_kernel<3><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, bp);
+    } else {
+      pack_a_kernel<6><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, ap);
+      CVS_CHECK_LAUNCH();
+      pack_b_kernel<6><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, bp);
+    }
     CVS_CHECK_LAUNCH();
-    pack_b_kernel<3><<<gb, 256, 0, s>>>(B, K, N, d.Np2, d.Kp, bp);
-  } else {
-    pack_a_kernel<6><<<ga, 256, 0, s>>>(A, M, K, d.Mp, d.Kp, ap);
+    CUtensorMap ma = make_map(ap, d.Mp, (int64_t)d.nseg * Kp, BM);
+    CUtensorMap mb = make_map(bp, d.Np2, (int64_t)d.nseg * Kp, BN);
+    const int nkt = d.nseg * Kp / BK;
+    int sp = tc_splits(tiles, nkt, 8);
+    if (part == nullptr || (size_t)sp * M * N > part_elems) sp = 1;
+    const int zkt = (nkt + sp - 1) / sp;
+    const int nz = (nkt + zkt - 1) / zkt;
+    const double beta_c = (k0 == 0) ? beta : 1.0;
+    dim3 grid(d.Np2 / BN, d.Mp / BM, nz);
+    const int tok = kstats_begin(s, K_TC_BF16X3, 8.0 * M * N * (double)Kc);
+    tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, nkt, zkt, M, N, alpha,
+                                                 beta_c, C, nz > 1 ? part : nullptr,
+                                                 err);
     CVS_CHECK_LAUNCH();
-    pack_b_kernel<6><<<gb, 256, 0, s>>>(B, K, N, d.Np2, d.Kp, bp);
+    kstats_end(s, tok);
+    if (nz > 1) splitk_reduce(s, M, N, nz, part, beta_c, C);
   }
-  CVS_CHECK_LAUNCH();
-  CUtensorMap ma = make_map(ap, d.Mp, (int64_t)d.nseg * d.Kp, BM);
-  CUtensorMap mb = make_map(bp, d.Np2, (int64_t)d.nseg * d.Kp, BN);
-  const int nkt = d.nseg * d.Kp / BK;
-  dim3 grid(d.Np2 / BN, d.Mp / BM);
-  tc_gemm_kernel<<<grid, 128, SMEM_BYTES, s>>>(ma, mb, nkt, M, N, alpha, beta,
-                                               C, err);
-  CVS_CHECK_LAUNCH();
 }
-
 
 // ===========================================================================
 // Exact-accumulation slice GEMM (an error-free splitting in the manner of
@@ -512,9 +552,9 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
 __global__ void __launch_bounds__(576, 1)
     tc_slice_kernel(const __grid_constant__ CUtensorMap tmA,
                     const __grid_constant__ CUtensorMap tmB, int npairs,
-                    int ktpp, int M, int N, const int* __restrict__ eA,
+                    int ktpp, int zl, int M, int N, const int* __restrict__ eA,
                     const int* __restrict__ eB, double alpha, double beta,
-                    View C, int* err) {
+                    View C, cplx* part, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -528,7 +568,11 @@ __global__ void __launch_bounds__(576, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * SBN;
-  const int runs_pp = (ktpp + RUN_KT - 1) / RUN_KT;
+  const int z = blockIdx.z;
+  // this CTA's k-tiles of every pair: [zb, ze) relative to the pair start
+  const int zb = z * zl, ze = min(ktpp, zb + zl);
+  const int zlen = max(0, ze - zb);
+  const int runs_pp = (zlen + RUN_KT - 1) / RUN_KT;
   const int nruns = npairs * runs_pp;
 
   if (threadIdx.x == 0) {
@@ -557,12 +601,13 @@ __global__ void __launch_bounds__(576, 1)
   const uint32_t tmem = *tslot;
 
   if (threadIdx.x == 0) {
-    // TMA producer over every k-tile of every pair
-    const int nkt = npairs * ktpp;
-    for (int kt = 0; kt < nkt; ++kt) {
-      const int s = kt % SSTAGES;
-      const uint32_t ph = (kt / SSTAGES) & 1;
-      if (kt >= SSTAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+    // TMA producer over this CTA's k-tiles of every pair
+    const int nkt = npairs * zlen;
+    for (int i = 0; i < nkt; ++i) {
+      const int kt = (i / zlen) * ktpp + zb + i % zlen;
+      const int s = i % SSTAGES;
+      const uint32_t ph = (i / SSTAGES) & 1;
+      if (i >= SSTAGES && !mbar_wait(&empty[s], ph ^ 1)) {
         fail = 1;
         break;
       }
@@ -574,11 +619,10 @@ __global__ void __launch_bounds__(576, 1)
   } else if (threadIdx.x == 32) {
     // MMA issuer: one exact run per (pair, run) into alternating buffers
     const uint32_t id = idesc_bf16(BM, SBN);
-    int kt = 0;
+    int i = 0;  // position in the producer's sequence
     for (int r = 0; r < nruns && !fail; ++r) {
-      const int p = r / runs_pp, rr = r % runs_pp;
-      const int kt0 = p * ktpp + rr * RUN_KT;
-      const int kt1 = min(p * ktpp + ktpp, kt0 + RUN_KT);
+      const int rr = r % runs_pp;
+      const int i0 = i, i1 = i + min(RUN_KT, zlen - rr * RUN_KT);
       const int b = r & 1;
       if (r >= 2 && !mbar_wait(&aempty[b], ((r >> 1) + 1) & 1)) {
         fail = 4;
@@ -586,9 +630,9 @@ __global__ void __launch_bounds__(576, 1)
       }
       fence_after();
       const uint32_t dt = tmem + (uint32_t)(b * SBN);
-      for (kt = kt0; kt < kt1; ++kt) {
-        const int s = kt % SSTAGES;
-        const uint32_t ph = (kt / SSTAGES) & 1;
+      for (i = i0; i < i1; ++i) {
+        const int s = i % SSTAGES;
+        const uint32_t ph = (i / SSTAGES) & 1;
         if (!mbar_wait(&full[s], ph)) {
           fail = 2;
           break;
@@ -598,7 +642,7 @@ __global__ void __launch_bounds__(576, 1)
         const uint64_t bd = sdesc(smem_u32(sB + s * S_B_TILE));
 #pragma unroll
         for (int kk = 0; kk < BK / 16; ++kk)
-          umma(dt, ad + 2 * kk, bd + 2 * kk, id, (kt != kt0 || kk) ? 1u : 0u);
+          umma(dt, ad + 2 * kk, bd + 2 * kk, id, (i != i0 || kk) ? 1u : 0u);
         umma_commit(&empty[s]);
       }
       umma_commit(&afull[b]);
@@ -643,16 +687,20 @@ __global__ void __launch_bounds__(576, 1)
     } else {
       const int m = m0 + q * 32 + lane;
       if (m < M) {
-        const int64_t ro = vrow(C, m);
+        const int64_t ro = part ? 0 : vrow(C, m);
         const double em = ldexp(1.0, eA[m]);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int n = (n0 + cq * 32) / 2 + i;
           if (n < N) {
             const double s = alpha * em * ldexp(1.0, eB[n]);
-            cplx* d = C.p + ro + vcol(C, n);
             cplx o = cmake(s * ((double)hi[2 * i] + (double)lo[2 * i]),
                            s * ((double)hi[2 * i + 1] + (double)lo[2 * i + 1]));
+            if (part) {
+              part[((int64_t)z * M + m) * N + n] = o;
+              continue;
+            }
+            cplx* d = C.p + ro + vcol(C, n);
             if (beta != 0.0) {
               cplx old = *d;
               o.x += beta * old.x;
@@ -673,12 +721,12 @@ __global__ void __launch_bounds__(576, 1)
 }
 
 // per-row (A: rows m, max over k) exponent: max |re|, |im| < 2^e
-__global__ void row_exp_kernel(View A, int M, int K, int* e) {
+__global__ void row_exp_kernel(View A, int M, int K, int k0, int* e) {
   for (int m = blockIdx.x; m < M; m += gridDim.x) {
     double mx = 0.0;
     const int64_t ro = vrow(A, m);
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      cplx a = A.p[ro + vcol(A, k)];
+      cplx a = A.p[ro + vcol(A, k0 + k)];
       mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
     }
     __shared__ double red[256];
@@ -694,12 +742,12 @@ __global__ void row_exp_kernel(View A, int M, int K, int* e) {
 }
 
 // per-column (B: columns n, max over k) exponent
-__global__ void col_exp_kernel(View B, int K, int N, int* e) {
+__global__ void col_exp_kernel(View B, int K, int k0, int N, int* e) {
   for (int n = blockIdx.x; n < N; n += gridDim.x) {
     double mx = 0.0;
     const int64_t co = vcol(B, n);
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      cplx b = B.p[vrow(B, k) + co];
+      cplx b = B.p[vrow(B, k0 + k) + co];
       mx = fmax(mx, fmax(fabs(b.x), fabs(b.y)));
     }
     __shared__ double red[256];
@@ -727,8 +775,9 @@ __device__ __forceinline__ void slices(double x, int e, __nv_bfloat16* q) {
 }
 
 template <int S>
-__global__ void slice_pack_a(View A, int M, int K, int Mp, int Kp, int npairs,
-                             const int* __restrict__ eA, __nv_bfloat16* out) {
+__global__ void slice_pack_a(View A, int M, int K, int k0, int Mp, int Kp,
+                             int npairs, const int* __restrict__ eA,
+                             __nv_bfloat16* out) {
   const int64_t ld = (int64_t)2 * npairs * Kp;
   const int64_t total = (int64_t)Mp * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -739,7 +788,7 @@ __global__ void slice_pack_a(View A, int M, int K, int Mp, int Kp, int npairs,
     if (m < M) {
       e = eA[m];
       if (k < K) {
-        a = A.p[vrow(A, m) + vcol(A, k)];
+        a = A.p[vrow(A, m) + vcol(A, k0 + k)];
         if (A.conj) a.y = -a.y;
       }
     }
@@ -755,8 +804,9 @@ __global__ void slice_pack_a(View A, int M, int K, int Mp, int Kp, int npairs,
 }
 
 template <int S>
-__global__ void slice_pack_b(View B, int K, int N, int Np2, int Kp, int npairs,
-                             const int* __restrict__ eB, __nv_bfloat16* out) {
+__global__ void slice_pack_b(View B, int K, int k0, int N, int Np2, int Kp,
+                             int npairs, const int* __restrict__ eB,
+                             __nv_bfloat16* out) {
   const int64_t ld = (int64_t)2 * npairs * Kp;
   const int64_t total = (int64_t)(Np2 / 2) * Kp;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -767,7 +817,7 @@ __global__ void slice_pack_b(View B, int K, int N, int Np2, int Kp, int npairs,
     if (n < N) {
       e = eB[n];
       if (k < K) {
-        b = B.p[vrow(B, k) + vcol(B, n)];
+        b = B.p[vrow(B, k0 + k) + vcol(B, n)];
         if (B.conj) b.y = -b.y;
       }
     }
@@ -787,17 +837,20 @@ __global__ void slice_pack_b(View B, int K, int N, int Np2, int Kp, int npairs,
 }
 
 struct SDims {
-  int Mp, Np2, Kp, npairs;
+  int Mp, Np2, npairs, kc;
   size_t a_bytes, b_bytes, e_bytes;
 };
 SDims sdims_of(int M, int N, int K, int nslices) {
   SDims d;
   d.Mp = (M + BM - 1) / BM * BM;
   d.Np2 = (2 * N + SBN - 1) / SBN * SBN;
-  d.Kp = (K + BK - 1) / BK * BK;
   d.npairs = nslices * (nslices + 1) / 2;
-  d.a_bytes = (size_t)d.Mp * 2 * d.npairs * d.Kp * 2;
-  d.b_bytes = (size_t)d.Np2 * 2 * d.npairs * d.Kp * 2;
+  const size_t per_k = (size_t)(d.Mp + d.Np2) * 2 * d.npairs * 2;
+  int64_t kc = (int64_t)(PACK_BUDGET / per_k) / BK * BK;
+  kc = std::max<int64_t>(kc, BK);
+  d.kc = (int)std::min<int64_t>(kc, ((int64_t)K + BK - 1) / BK * BK);
+  d.a_bytes = (size_t)d.Mp * 2 * d.npairs * d.kc * 2;
+  d.b_bytes = (size_t)d.Np2 * 2 * d.npairs * d.kc * 2;
   d.e_bytes = ((size_t)d.Mp + d.Np2 / 2 + 64) * sizeof(int);
   return d;
 }
@@ -827,7 +880,7 @@ size_t slice_workspace_bytes(int M, int N, int K, int nslices) {
 
 void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
                  double alpha, View A, View B, double beta, View C, void* work,
-                 size_t work_bytes, int* err) {
+                 size_t work_bytes, cplx* part, size_t part_elems, int* err) {
   if (M <= 0 || N <= 0) return;
   CVS_REQUIRE(nslices == 4 || nslices == 7, -1, "zgemm_slice: 4 or 7 slices");
   SDims d = sdims_of(M, N, K, nslices);
@@ -845,30 +898,44 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
   __nv_bfloat16* bp = (__nv_bfloat16*)((char*)work + d.a_bytes);
   int* eA = (int*)((char*)work + d.a_bytes + d.b_bytes);
   int* eB = eA + d.Mp;
-  row_exp_kernel<<<std::min(M, 152 * 16), 256, 0, s>>>(A, M, K, eA);
-  CVS_CHECK_LAUNCH();
-  col_exp_kernel<<<std::min(N, 152 * 16), 256, 0, s>>>(B, K, N, eB);
-  CVS_CHECK_LAUNCH();
-  const unsigned ga = grid1d((int64_t)d.Mp * d.Kp, 256);
-  const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * d.Kp, 256);
-  if (nslices == 4) {
-    slice_pack_a<4><<<ga, 256, 0, s>>>(A, M, K, d.Mp, d.Kp, d.npairs, eA, ap);
+  const int64_t tiles = (int64_t)(d.Np2 / SBN) * (d.Mp / BM);
+  for (int k0 = 0; k0 < K; k0 += d.kc) {
+    const int Kc = std::min(d.kc, K - k0);
+    const int Kp = (Kc + BK - 1) / BK * BK;
+    row_exp_kernel<<<std::min(M, 152 * 16), 256, 0, s>>>(A, M, Kc, k0, eA);
     CVS_CHECK_LAUNCH();
-    slice_pack_b<4><<<gb, 256, 0, s>>>(B, K, N, d.Np2, d.Kp, d.npairs, eB, bp);
-  } else {
-    slice_pack_a<7><<<ga, 256, 0, s>>>(A, M, K, d.Mp, d.Kp, d.npairs, eA, ap);
+    col_exp_kernel<<<std::min(N, 152 * 16), 256, 0, s>>>(B, Kc, k0, N, eB);
     CVS_CHECK_LAUNCH();
-    slice_pack_b<7><<<gb, 256, 0, s>>>(B, K, N, d.Np2, d.Kp, d.npairs, eB, bp);
+    const unsigned ga = grid1d((int64_t)d.Mp * Kp, 256);
+    const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * Kp, 256);
+    if (nslices == 4) {
+      slice_pack_a<4><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, d.npairs, eA, ap);
+      CVS_CHECK_LAUNCH();
+      slice_pack_b<4><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eB, bp);
+    } else {
+      slice_pack_a<7><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, d.npairs, eA, ap);
+      CVS_CHECK_LAUNCH();
+      slice_pack_b<7><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eB, bp);
+    }
+    CVS_CHECK_LAUNCH();
+    const int64_t kcols = (int64_t)2 * d.npairs * Kp;
+    CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
+    CUtensorMap mb = make_map(bp, d.Np2, kcols, SBN);
+    const int ktpp = 2 * Kp / BK;
+    int sp = tc_splits(tiles, ktpp, RUN_KT);
+    if (part == nullptr || (size_t)sp * M * N > part_elems) sp = 1;
+    const int zl = (ktpp + sp - 1) / sp;
+    const int nz = (ktpp + zl - 1) / zl;
+    const double beta_c = (k0 == 0) ? beta : 1.0;
+    dim3 grid(d.Np2 / SBN, d.Mp / BM, nz);
+    const int tok = kstats_begin(s, K_TC_SLICE, 8.0 * M * N * (double)Kc);
+    tc_slice_kernel<<<grid, 576, S_SMEM, s>>>(ma, mb, d.npairs, ktpp, zl, M, N,
+                                              eA, eB, alpha, beta_c, C,
+                                              nz > 1 ? part : nullptr, err);
+    CVS_CHECK_LAUNCH();
+    kstats_end(s, tok);
+    if (nz > 1) splitk_reduce(s, M, N, nz, part, beta_c, C);
   }
-  CVS_CHECK_LAUNCH();
-  const int64_t kcols = (int64_t)2 * d.npairs * d.Kp;
-  CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
-  CUtensorMap mb = make_map(bp, d.Np2, kcols, SBN);
-  const int ktpp = 2 * d.Kp / BK;
-  dim3 grid(d.Np2 / SBN, d.Mp / BM);
-  tc_slice_kernel<<<grid, 576, S_SMEM, s>>>(ma, mb, d.npairs, ktpp, M, N, eA,
-                                            eB, alpha, beta, C, err);
-  CVS_CHECK_LAUNCH();
 }
 
 }  // namespace cvs

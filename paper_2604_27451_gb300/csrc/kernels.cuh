@@ -7,8 +7,15 @@ namespace cvs {
 
 // ------------------------------------------------------------- GEMMs
 // C = alpha * A * B + beta * C, complex, two-mode views, batch over z.
+// `part` (part_elems complex) is scratch for split-K partial products; with
+// part == nullptr the kernel runs without splitting.
 void zgemm_f64(cudaStream_t s, int M, int N, int K, double alpha, View A,
-               View B, double beta, View C, int batch = 1);
+               View B, double beta, View C, int batch = 1,
+               cplx* part = nullptr, size_t part_elems = 0);
+// C(m, n) = sum_z part[z][m][n] + beta * C(m, n), part dense [nz][M][N]
+void splitk_reduce(cudaStream_t s, int M, int N, int nz, const cplx* part,
+                   double beta, View C);
+void init_gemm_attributes();
 
 // Same contract on the tcgen05 tensor cores: A and B are split into bf16
 // parts, nprod = 3 (hi/lo, BF16x3) or 6 (hi/mid/lo, BF16x6) products per
@@ -18,7 +25,7 @@ void zgemm_f64(cudaStream_t s, int M, int N, int K, double alpha, View A,
 size_t tc_workspace_bytes(int M, int N, int K, int nprod);
 void zgemm_tc(cudaStream_t s, int nprod, int M, int N, int K, double alpha,
               View A, View B, double beta, View C, void* work,
-              size_t work_bytes, int* err);
+              size_t work_bytes, cplx* part, size_t part_elems, int* err);
 bool tc_available();
 // Exact-accumulation slice GEMM on the tensor cores (see gemm_tc.cu):
 // nslices = 4 (10 slice products, ~2^-28 of row max x column max) or 7
@@ -26,7 +33,7 @@ bool tc_available();
 size_t slice_workspace_bytes(int M, int N, int K, int nslices);
 void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
                  double alpha, View A, View B, double beta, View C, void* work,
-                 size_t work_bytes, int* err);
+                 size_t work_bytes, cplx* part, size_t part_elems, int* err);
 
 // C = beta * C over a view
 void scale_view(cudaStream_t s, int M, int N, double beta, View C, int batch);
@@ -100,8 +107,18 @@ void k_smallest(cudaStream_t s, const double* d, int64_t N, int k,
                 int64_t* idx_dev, double* work);
 // make the largest-modulus entry of each of k vectors real positive
 void phase_fix(cudaStream_t s, cplx* x, int k, int64_t N, double* work);
-// A = (H + H^H)/2 for an m x m block of H (leading dimension ldh)
-void hermitize(cudaStream_t s, const cplx* H, int ldh, int m, cplx* A);
+// A = (H + H^H)/2 for an m x m block of H (leading dimension ldh); entries
+// H[i][j] with j < jdone <= i were not computed and are taken from the
+// Hermitian partner (jdone = m when every entry is present)
+void hermitize(cudaStream_t s, const cplx* H, int ldh, int m, cplx* A,
+               int jdone);
+// H[i][j] = conj(H[j][i]) for i0 <= i < i1, j < i0
+void herm_fill(cudaStream_t s, cplx* H, int ldh, int i0, int i1);
+// transform X (cnt x kept) making the block with Gram matrix G orthonormal
+void block_orth(cudaStream_t s, const cplx* G, int ldg, int cnt,
+                const double* norm0, double tol, cplx* X, int* kept);
+void gram_diag_sqrt(cudaStream_t s, const cplx* G, int ldg, int cnt,
+                    double* out);
 // X[r][c] *= sc[r] (device scale vector)
 void scale_rows(cudaStream_t s, cplx* X, int rows, int cols, int ld,
                 const double* sc);

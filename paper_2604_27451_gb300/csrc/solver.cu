@@ -40,6 +40,9 @@
 #include "common.cuh"
 #include "kernels.cuh"
 
+namespace cvs {
+unsigned long long g_launch_count = 0;
+}
 using namespace cvs;
 
 namespace {
@@ -153,6 +156,7 @@ struct cvsadc_ctx {
   DBuf s_big1, s_big2, s_S, s_R, s_Y, s_V, s_part, s_small, s_tc;
   DBuf dv_V, dv_W, dv_X, dv_AX, dv_T, dv_H, dv_A, dv_U, dv_w, dv_misc;
   DBuf err;  // device int: non-zero after a bounded device wait expired
+  DBuf s_kpart;  // split-K partial products
 
   void sync() { CVS_CUDA(cudaStreamSynchronize(stream)); }
 };
@@ -179,8 +183,10 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
   check_view(C, M, N, batch, "C");
   // the tensor-core path pays a packing pass per operand: keep it for
   // contractions with enough work per packed element
-  const bool tc = prec != CVSADC_FP64 && M >= 64 && N >= 32 && K >= 64 &&
-                  (double)M * N * K >= 1e7;
+  // small outputs with a long K: all dot products at once, FP64
+  const bool small = (int64_t)M * N <= 4096 && M + N <= 384 && K >= 4096;
+  const bool tc = !small && prec != CVSADC_FP64 && M >= 32 && N >= 16 &&
+                  K >= 64 && (double)M * N * K >= 1e7;
   if (tc) {
     CVS_REQUIRE(tc_available(), CVSADC_EINVAL,
                 "tensor-core precisions need an sm_103 GPU with tcgen05");
@@ -197,14 +203,17 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
       if (cc.ext >= 0) cc.ext -= z * C.batch;
       if (ns)
         zgemm_slice(c->stream, ns, M, N, K, alpha, a, b, beta, cc, c->s_tc.p,
-                    need, c->err.as<int>());
+                    need, c->s_kpart.c(), c->s_kpart.bytes / sizeof(cplx),
+                    c->err.as<int>());
       else
         zgemm_tc(c->stream, 3, M, N, K, alpha, a, b, beta, cc, c->s_tc.p, need,
+                 c->s_kpart.c(), c->s_kpart.bytes / sizeof(cplx),
                  c->err.as<int>());
     }
     return;
   }
-  zgemm_f64(c->stream, M, N, K, alpha, A, B, beta, C, batch);
+  zgemm_f64(c->stream, M, N, K, alpha, A, B, beta, C, batch, c->s_kpart.c(),
+            c->s_kpart.bytes / sizeof(cplx));
 }
 
 void gemm64(cvsadc_ctx* c, int M, int N, int K, double alpha, View A,
@@ -215,7 +224,8 @@ void gemm64(cvsadc_ctx* c, int M, int N, int K, double alpha, View A,
   check_view(A, M, K, batch, "A");
   check_view(B, K, N, batch, "B");
   check_view(C, M, N, batch, "C");
-  zgemm_f64(c->stream, M, N, K, alpha, A, B, beta, C, batch);
+  zgemm_f64(c->stream, M, N, K, alpha, A, B, beta, C, batch, c->s_kpart.c(),
+            c->s_kpart.bytes / sizeof(cplx));
 }
 
 void copyv(cvsadc_ctx* c, int M, int N, double alpha, View src, View dst) {
@@ -374,70 +384,82 @@ void build_moments(cvsadc_ctx* c, int prec) {
 }
 
 // ----------------------------------------------------------------- sigma
-void sigma_impl(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int nvec) {
+// sigma for a group of g vectors at once: every contraction runs over the
+// whole group, so the ncore-sized dimensions become g * ncore and operands
+// built from B^P are packed once per group.
+void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g) {
   const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
             L = c->naux;
   const int64_t nn = (int64_t)n * n, N1 = c->N1, N = c->N;
-  const int64_t wv = (int64_t)nw * v, vL = (int64_t)v * L;
+  const int64_t wv = (int64_t)nw * v, vL = (int64_t)v * L, wvL = wv * L;
+  const int64_t N1L = N1 * L, N1wv = N1 * wv;
   const cplx* B = c->B.c();
-  size_t big = (size_t)N1 * wv * sizeof(cplx);
-  c->s_big1.ensure(big);
-  c->s_big2.ensure(big);
-  c->s_S.ensure((size_t)N1 * L * sizeof(cplx));
-  c->s_R.ensure((size_t)wv * L * sizeof(cplx));
-  c->s_Y.ensure((size_t)N1 * L * sizeof(cplx));
-  c->s_V.ensure((size_t)wv * L * sizeof(cplx));
-  cplx* Yt = c->s_big1.c();
-  cplx* G = c->s_big2.c();
-  cplx* S = c->s_S.c();
-  cplx* R = c->s_R.c();
-  cplx* Y = c->s_Y.c();
-  cplx* Vv = c->s_V.c();
-  for (int q = 0; q < nvec; ++q) {
-    const cplx* x1 = x + q * N;
-    const cplx* x2 = x1 + N1;
-    cplx* s1 = sig + q * N;
-    cplx* s2 = s1 + N1;
-    unpack_doubles(c->stream, x2, nc, nw, v, Yt);
-    // S[(I,a)][P] = sum_{jb} y_{Ijab} B^P_{jb}
-    gemm(c, prec, (int)N1, L, (int)wv, 1.0, view(Yt, wv, 1),
-         rows2(view(B + (int64_t)nc * n + o, 0, nn), n, 1, v), 0.0,
-         view(S, L, 1));
-    // R[(c,j)][P] = sum_{Ib} y_{Ijcb} B^P_{Ib}
-    gemm(c, prec, (int)wv, L, (int)N1, 1.0,
-         cols2(view(Yt, v, 0), wv * v, 1, v),
-         rows2(view(B + o, 0, nn), n, 1, v), 0.0, view(R, L, 1));
-    // sigma1 (M12 x2)
-    gemm(c, prec, nc, v, (int)vL, -1.0, view(S, vL, 1),
-         rows2(view(B + (int64_t)o * n + o, 0, n), 1, nn, L), 0.0,
-         view(s1, v, 1));
-    gemm(c, prec, nc, v, nc * L, 1.0, cols2(view(B, 1, 0), n, nn, L),
-         rows2(view(S, 0, L), vL, 1, L), 1.0, view(s1, v, 1));
-    gemm(c, prec, nc, v, nw * L, -1.0,
-         cols2(view(B + (int64_t)nc * n, 1, 0), n, nn, L),
-         view(R, 1, (int64_t)nw * L), 1.0, view(s1, v, 1));
-    // Y[(I,a)][P] = sum_c x_Ic B^P_ac - sum_K x_Ka B^P_KI
-    gemm(c, prec, nc, (int)vL, v, 1.0, view(x1, v, 1),
-         cols2(view(B + (int64_t)o * n + o, 1, 0), n, nn, L), 0.0,
-         view(Y, vL, 1));
-    gemm(c, prec, v, nc * L, nc, -1.0, view(x1, 1, v),
-         cols2(view(B, n, 0), 1, nn, L), 1.0,
-         cols2(view(Y, L, 0), vL, 1, L));
-    // Vv[(j,b)][P] = sum_K x_Kb B^P_{K j}
-    gemm(c, prec, v, nw * L, nc, 1.0, view(x1, 1, v),
-         cols2(view(B + nc, n, 0), 1, nn, L), 0.0,
-         cols2(view(Vv, L, 0), vL, 1, L));
-    // G[(I,a)][(j,b)] = sum_P Y B^P_{bj} - sum_P B^P_{aI} Vv
-    gemm(c, prec, (int)N1, (int)wv, L, 1.0, view(Y, L, 1),
-         cols2(view(B + (int64_t)o * n + nc, nn, 0), 1, n, v), 0.0,
-         view(G, wv, 1));
-    gemm(c, prec, (int)N1, (int)wv, L, -1.0,
-         rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v), view(Vv, 1, L),
-         1.0, view(G, wv, 1));
-    sigma2_finish(c->stream, G, x2, c->eps.d(), nc, nw, v, s2);
-    // sigma1 += M11 x1 (dense product, FP64 path for the small block)
-    gemm64(c, (int)N1, 1, (int)N1, 1.0, view(c->M11.c(), N1, 1),
-              view(x1, 1, 0), 1.0, view(s1, 1, 0));
+  c->s_big1.ensure((size_t)g * N1wv * sizeof(cplx));
+  c->s_big2.ensure((size_t)g * N1wv * sizeof(cplx));
+  c->s_S.ensure((size_t)g * N1L * sizeof(cplx));
+  c->s_R.ensure((size_t)g * wvL * sizeof(cplx));
+  c->s_Y.ensure((size_t)g * N1L * sizeof(cplx));
+  c->s_V.ensure((size_t)g * wvL * sizeof(cplx));
+  cplx* Yt = c->s_big1.c();  // [q][I][a][j][b]
+  cplx* G = c->s_big2.c();   // [q][(I,a)][(j,b)]
+  cplx* S = c->s_S.c();      // [(q,I,a)][P]
+  cplx* R = c->s_R.c();      // [(q,c,j)][P]
+  cplx* Y = c->s_Y.c();      // [(q,I,a)][P]
+  cplx* Vv = c->s_V.c();     // [(q,j,b)][P]
+  for (int q = 0; q < g; ++q)
+    unpack_doubles(c->stream, x + q * N + N1, nc, nw, v, Yt + q * N1wv);
+  // S[(q,I,a)][P] = sum_{jb} y_{Ijab} B^P_{jb}
+  gemm(c, prec, (int)(g * N1), L, (int)wv, 1.0, view(Yt, wv, 1),
+       rows2(view(B + (int64_t)nc * n + o, 0, nn), n, 1, v), 0.0,
+       view(S, L, 1));
+  // R[(q,c,j)][P] = sum_{Ib} y_{Ijcb} B^P_{Ib}
+  gemm(c, prec, (int)(g * wv), L, (int)N1,
+       1.0, cols2(rows2(view(Yt, 0, 0), N1wv, v, (int)wv), wv * v, 1, v),
+       rows2(view(B + o, 0, nn), n, 1, v), 0.0, view(R, L, 1));
+  // sigma1 (M12 x2): rows (q, K), columns c
+  const View s1rows = rows2(view(sig, 0, 1), N, v, nc);
+  gemm(c, prec, g * nc, v, (int)vL, -1.0, view(S, vL, 1),
+       rows2(view(B + (int64_t)o * n + o, 0, n), 1, nn, L), 0.0, s1rows);
+  const View s1cols = cols2(view(sig, v, 0), N, 1, v);  // (K, (q,c))
+  gemm(c, prec, nc, g * v, nc * L, 1.0, cols2(view(B, 1, 0), n, nn, L),
+       cols2(rows2(view(S, 0, 0), vL, 1, L), N1L, L, v), 1.0, s1cols);
+  gemm(c, prec, nc, g * v, nw * L, -1.0,
+       cols2(view(B + (int64_t)nc * n, 1, 0), n, nn, L),
+       cols2(view(R, 1, 0), wvL, (int64_t)nw * L, v), 1.0, s1cols);
+  // Y[(q,I,a)][P] = sum_c x_Ic B^P_ac - sum_K x_Ka B^P_KI
+  gemm(c, prec, g * nc, (int)vL, v, 1.0, rows2(view(x, 0, 1), N, v, nc),
+       cols2(view(B + (int64_t)o * n + o, 1, 0), n, nn, L), 0.0,
+       view(Y, vL, 1));
+  gemm(c, prec, g * v, nc * L, nc, -1.0, rows2(view(x, 0, v), N, 1, v),
+       cols2(view(B, n, 0), 1, nn, L), 1.0,
+       cols2(rows2(view(Y, 0, 0), N1L, L, v), vL, 1, L));
+  // Vv[(q,j,b)][P] = sum_K x_Kb B^P_{K j}
+  gemm(c, prec, g * v, nw * L, nc, 1.0, rows2(view(x, 0, v), N, 1, v),
+       cols2(view(B + nc, n, 0), 1, nn, L), 0.0,
+       cols2(rows2(view(Vv, 0, 0), wvL, L, v), vL, 1, L));
+  // G[q][(I,a)][(j,b)] = sum_P Y B^P_{bj} - sum_P B^P_{aI} Vv
+  gemm(c, prec, (int)(g * N1), (int)wv, L, 1.0, view(Y, L, 1),
+       cols2(view(B + (int64_t)o * n + nc, nn, 0), 1, n, v), 0.0,
+       view(G, wv, 1));
+  gemm(c, prec, (int)N1, (int)(g * wv), L, -1.0,
+       rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v), view(Vv, 1, L), 1.0,
+       cols2(view(G, wv, 0), N1wv, 1, (int)wv));
+  for (int q = 0; q < g; ++q)
+    sigma2_finish(c->stream, G + q * N1wv, x + q * N + N1, c->eps.d(), nc, nw,
+                  v, sig + q * N + N1);
+  // sigma1 += M11 x1 (dense product, FP64 for the small block)
+  gemm64(c, (int)N1, g, (int)N1, 1.0, view(c->M11.c(), N1, 1), view(x, 1, N),
+         1.0, view(sig, 1, N));
+}
+
+void sigma_impl(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int nvec) {
+  const int64_t N1 = c->N1, wv = (int64_t)c->nval * c->nvirt, L = c->naux;
+  const double per_vec = (2.0 * N1 * wv + 2.0 * N1 * L + 2.0 * wv * L) * sizeof(cplx);
+  const double budget = 48e9;
+  int g = (int)std::max(1.0, std::min((double)nvec, budget / per_vec));
+  for (int q0 = 0; q0 < nvec; q0 += g) {
+    const int gg = std::min(g, nvec - q0);
+    sigma_group(c, prec, x + q0 * c->N, sig + q0 * c->N, gg);
   }
 }
 
@@ -465,7 +487,7 @@ void build_fns(cvsadc_ctx* c, int prec, double tau) {
   A.ensure(vv * sizeof(cplx));
   Vec.ensure(vv * sizeof(cplx));
   w.ensure(v * sizeof(double) + 64);
-  hermitize(c->stream, D.c(), v, v, A.c());
+  hermitize(c->stream, D.c(), v, v, A.c(), v);
   c->s_small.ensure(4096);
   jacobi_eigh(c->stream, A.c(), v, w.d(), Vec.c(), 40, c->s_small.d());
   std::vector<double> occ_asc(v);
@@ -502,7 +524,7 @@ void build_fns(cvsadc_ctx* c, int prec, double tau) {
   Fh.ensure((size_t)vk * vk * sizeof(cplx));
   Z.ensure((size_t)vk * vk * sizeof(cplx));
   et.ensure(vk * sizeof(double) + 64);
-  hermitize(c->stream, Fns.c(), vk, vk, Fh.c());
+  hermitize(c->stream, Fns.c(), vk, vk, Fh.c(), vk);
   jacobi_eigh(c->stream, Fh.c(), vk, et.d(), Z.c(), 40, c->s_small.d());
   // U = V~ Z~ (Eq. 20)
   c->fns_U.ensure((size_t)v * vk * sizeof(cplx));
@@ -640,6 +662,7 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
 struct DavResult {
   int iters = 0, sigmas = 0, converged = 0;
   double maxres = 0.0;
+  double t_sigma_ms = 0.0;
 };
 
 // Block Davidson for the lowest nroots eigenpairs of M (sigma in `prec`,
@@ -670,15 +693,17 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
   // dv_misc: ts_dot partials [msub*msub*TS_CHUNKS] complex, then a
   // double work area laid out at fixed offsets
   const size_t W_PART = 0, W_RN2 = 64 * 320, W_JAC = W_RN2 + 128,
-               W_KS = W_JAC + 64, W_IDX = W_KS + 1024, W_COEF = W_IDX + 128,
-               W_TOTAL = W_COEF + 4 * 256;
+               W_KS = W_JAC + 64, W_IDX = W_KS + 1024, W_NRM = W_IDX + 128,
+               W_KEPT = W_NRM + 64, W_COEF = W_KEPT + 64,
+               W_TOTAL = W_COEF + 2 * (2 * 64 * 64 + 128 * 64);
   c->dv_misc.ensure((size_t)msub * msub * TS_CHUNKS * sizeof(cplx) +
                     W_TOTAL * sizeof(double));
   cplx* V = c->dv_V.c();
   cplx* W = c->dv_W.c();
   cplx* part = c->dv_misc.c();
   double* dwork = (double*)(part + (size_t)msub * msub * TS_CHUNKS);
-  cplx* coef = (cplx*)(dwork + W_COEF);  // up to 512 complex scalars
+  cplx* coef = (cplx*)(dwork + W_COEF);  // Gram, transform, projections
+  cplx* Cproj = coef + 2 * 64 * 64;       // [msub][64] projection coefficients
   cudaStream_t s = c->stream;
 
   // initial vectors: given X0, else unit vectors at the smallest diagonal
@@ -702,49 +727,35 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
       CVS_CUDA(cudaMemcpyAsync(V + q * N + hidx[q], &one, sizeof(cplx),
                                cudaMemcpyHostToDevice, s));
   }
-  // orthonormalise the starting block (two-pass classical Gram-Schmidt)
-  auto orthonormalise_append = [&](const cplx* src, int cnt) {
-    int added = 0;
-    std::vector<cplx> nrm(1);
-    for (int q = 0; q < cnt; ++q) {
-      cplx* dst = V + (int64_t)m * N;
-      if (dst != src + (int64_t)q * N)
-        CVS_CUDA(cudaMemcpyAsync(dst, src + (int64_t)q * N, N * sizeof(cplx),
-                                 cudaMemcpyDeviceToDevice, s));
-      double n0 = 0;
-      {
-        cplx* out = coef;
-        ts_dot(s, dst, 1, dst, 1, N, part, out, 1);
-        CVS_CUDA(cudaMemcpyAsync(nrm.data(), out, sizeof(cplx),
-                                 cudaMemcpyDeviceToHost, s));
-        c->sync();
-        n0 = std::sqrt(std::max(nrm[0].x, 0.0));
-      }
-      if (m > 0) {
-        for (int pass = 0; pass < 2; ++pass) {
-          cplx* cf = coef;
-          ts_dot(s, V, m, dst, 1, N, part, cf, 1);
-          ts_subtract(s, V, m, cf, 1, 1, N, dst);
-        }
-      }
-      cplx* out = coef;
-      ts_dot(s, dst, 1, dst, 1, N, part, out, 1);
-      CVS_CUDA(cudaMemcpyAsync(nrm.data(), out, sizeof(cplx),
-                               cudaMemcpyDeviceToHost, s));
-      c->sync();
-      double nr = std::sqrt(std::max(nrm[0].x, 0.0));
-      if (nr > 1e-8 * std::max(n0, 1e-300) && nr > 1e-300) {
-        double sc = 1.0 / nr;
-        CVS_CUDA(cudaMemcpyAsync(dwork + W_KS, &sc, sizeof(double),
-                                 cudaMemcpyHostToDevice, s));
-        scale_vectors(s, dst, dwork + W_KS, 1, N);
-        c->sync();  // sc lives on the host stack
-        ++m;
-        ++added;
-        if (m >= msub) break;
+  // append a block of cnt vectors (contiguous at T) to V: two passes of
+  // block classical Gram-Schmidt against V, then an orthonormalising
+  // transform of the block from its Gram matrix (FP64 throughout); vectors
+  // whose norm falls below 1e-8 of their original norm are dropped
+  cplx* G0 = coef;                     // [64][64] Gram matrix
+  cplx* Xo = coef + 64 * 64;           // [64][64] transform
+  double* nrm0 = dwork + W_NRM;        // [64]
+  int* kept_d = (int*)(dwork + W_KEPT);
+  auto orthonormalise_append = [&](cplx* T, int cnt) {
+    cnt = std::min(cnt, msub - m);
+    if (cnt <= 0) return 0;
+    ts_dot(s, T, cnt, T, cnt, N, part, G0, cnt);
+    gram_diag_sqrt(s, G0, cnt, cnt, nrm0);
+    if (m > 0) {
+      for (int pass = 0; pass < 2; ++pass) {
+        ts_dot(s, V, m, T, cnt, N, part, Cproj, cnt);
+        ts_subtract(s, V, m, Cproj, cnt, cnt, N, T);
       }
     }
-    return added;
+    ts_dot(s, T, cnt, T, cnt, N, part, G0, cnt);
+    block_orth(s, G0, cnt, cnt, nrm0, 1e-8, Xo, kept_d);
+    int kept = 0;
+    CVS_CUDA(cudaMemcpyAsync(&kept, kept_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    c->sync();
+    if (kept > 0)
+      ts_combine(s, T, Xo, nullptr, nullptr, cnt, cnt, kept, N,
+                 V + (int64_t)m * N);
+    m += kept;
+    return kept;
   };
   {
     // guesses live in V already at slots [0, nguess): compact through W
@@ -759,19 +770,21 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
   for (int it = 0; it < max_iter; ++it) {
     // sigma for new vectors
     int nnew = m - m_done;
+    cudaEvent_t e0, e1;
+    CVS_CUDA(cudaEventCreate(&e0));
+    CVS_CUDA(cudaEventCreate(&e1));
+    CVS_CUDA(cudaEventRecord(e0, s));
     sigma_impl(c, prec, V + (int64_t)m_done * N, W + (int64_t)m_done * N, nnew);
+    CVS_CUDA(cudaEventRecord(e1, s));
     res.sigmas += nnew;
     // subspace matrix columns for the new vectors
     ts_dot(s, V, m, W + (int64_t)m_done * N, nnew, N, part,
            c->dv_H.c() + m_done, msub);
-    // rows for the new vectors against old sigma (Hermitian completion is
-    // done from both triangles; fill the remaining block)
-    if (m_done > 0)
-      ts_dot(s, V + (int64_t)m_done * N, nnew, W, m_done, N, part,
-             c->dv_H.c() + (int64_t)m_done * msub, msub);
+    // the new rows against the old sigma images follow from Hermiticity
+    herm_fill(s, c->dv_H.c(), msub, m_done, m);
     m_done = m;
     // A = (H + H^H)/2 over m x m (H stored with leading dimension msub)
-    hermitize(s, c->dv_H.c(), msub, m, c->dv_A.c());
+    hermitize(s, c->dv_H.c(), msub, m, c->dv_A.c(), m);
     jacobi_eigh(s, c->dv_A.c(), m, c->dv_w.d(), c->dv_U.c(), 60,
                 dwork + W_JAC);
     // Ritz vectors and their sigma images for the lowest k
@@ -784,6 +797,13 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     CVS_CUDA(cudaMemcpyAsync(rn2.data(), dwork + W_RN2, k * sizeof(double),
                              cudaMemcpyDeviceToHost, s));
     c->sync();
+    {
+      float ms = 0;
+      CVS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      res.t_sigma_ms += ms;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
     res.iters = it + 1;
     if (verbose()) {
       double mx = 0;
@@ -804,8 +824,12 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     }
     if (todo.empty() || it == max_iter - 1) break;
     if (stop_on_stagnation) {
+      // near the noise floor of a mixed-precision sigma the residual stops
+      // falling: end when it has not halved over 30 iterations there
       hist.push_back(res.maxres);
-      if (hist.size() > 50 && res.maxres > 0.5 * hist[hist.size() - 51]) break;
+      if (res.maxres < 100 * tol && hist.size() > 30 &&
+          res.maxres > 0.5 * hist[hist.size() - 31])
+        break;
     }
     // thick restart to the nkeep lowest Ritz vectors when the block does
     // not fit
@@ -851,6 +875,15 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
 // Residual at which the mixed-precision Davidson hands over to the FP64
 // correction: a few times the sigma noise of the tensor-core GEMMs
 // (BF16X3 ~1e-5 relative, SLICE4 ~1e-8, on |M x| of O(10-100) Eh).
+// FP64-class sigma for the residual correction: the exact-slice
+// tensor-core GEMM (FP64_SLICE7, ~1e-14 relative) after SLICE4, the FP64
+// FMA GEMM after BF16X3 (CVSADC_REFINE_FP64 forces FP64 FMA for both)
+int refine_precision(int prec) {
+  const char* e = getenv("CVSADC_REFINE_FP64");
+  if (e && *e && *e != '0') return CVSADC_FP64;
+  return prec == CVSADC_MIXED_SLICE4 ? CVSADC_FP64_SLICE7 : CVSADC_FP64;
+}
+
 double mixed_tolerance(int prec) {
   const char* e = getenv("CVSADC_MIXED_TOL");
   if (e && *e) return atof(e);
@@ -889,10 +922,12 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
     CVS_CUDA(cudaMemcpyAsync(X0.p, Xd.p, (size_t)k * c->N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, c->stream));
     int sweeps = p->refine_sweeps > 0 ? p->refine_sweeps : 2;
-    DavResult r2 = davidson_impl(c, CVSADC_FP64, k, sweeps, max_sub, tol, X0.c(),
-                                 k, Xd.c(), w.data());
+    const int rprec = refine_precision(p->precision);
+    DavResult r2 = davidson_impl(c, rprec, k, sweeps, max_sub, tol, X0.c(), k,
+                                 Xd.c(), w.data());
     r.iters += r2.iters;
     r.sigmas += r2.sigmas;
+    r.t_sigma_ms += r2.t_sigma_ms;
     r.converged = r2.converged;
     r.maxres = r2.maxres;
     t_ref = now_ms() - t1;
@@ -937,6 +972,7 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
     info->max_residual = r.maxres;
     info->t_davidson_ms = t1 - t0;
     info->t_refine_ms = t_ref;
+    info->t_sigma_ms = r.t_sigma_ms;
     info->emp2 = c->emp2;
     info->nvirt_kept = c->nvirt;
   }
@@ -996,6 +1032,8 @@ int cvsadc_create(cvsadc_ctx** ctx, int device, void* cuda_stream) {
   c->device = device;
   int rc = guarded(c, [&] {
     init_kernel_attributes();
+    init_gemm_attributes();
+    c->s_kpart.ensure((size_t)8 << 20 << 4);  // 8 Mi complex = 128 MB
     c->err.ensure(256);
     CVS_CUDA(cudaMemset(c->err.p, 0, 256));
     if (cuda_stream) {
@@ -1122,6 +1160,26 @@ int cvsadc_sigma(cvsadc_ctx* c, int32_t precision, int32_t flags,
     }
     c->sync();
   });
+}
+
+void cvsadc_kernel_timing(int32_t enable) { kstats_set(enable != 0); }
+
+int cvsadc_kernel_stats(int32_t kernel, int64_t* launches, double* ms,
+                        double* flops) {
+  if (kernel < 0 || kernel >= K_NKERNELS || !launches || !ms || !flops)
+    return CVSADC_EINVAL;
+  return guarded(nullptr, [&] { kstats_collect(kernel, launches, ms, flops); });
+}
+
+void cvsadc_kernel_stats_reset(void) {
+  try {
+    kstats_reset();
+  } catch (...) {
+  }
+}
+
+int64_t cvsadc_launch_count(void) {
+  return (int64_t)__atomic_load_n(&g_launch_count, __ATOMIC_RELAXED);
 }
 
 int cvsadc_zgemm(cvsadc_ctx* c, int32_t precision, int32_t flags, int32_t M,
