@@ -225,6 +225,40 @@ int cvsadc_kernel_stats(int32_t kernel, int64_t* launches, double* ms,
                         double* flops);
 void cvsadc_kernel_stats_reset(void);
 
+/* --------------------------------------------------------------------
+ * Allocation-free small-output GEMM.  The paper has no counterpart: this
+ * is a service for callers that must not let a library allocate device
+ * memory -- a process whose device memory is already reserved by another
+ * allocator (a framework's caching allocator, a pre-sized pool), where an
+ * extra cudaMalloc fails or fragments that pool, or a latency-sensitive
+ * loop that cannot take the implicit synchronisation of cudaMalloc and
+ * cudaFree.
+ *
+ * C = A B, complex128, row-major, all three device pointers on the current
+ * device: A [M][lda], B [K][ldb], C [M][ldc], with M * N <= 4096 and
+ * M + N <= 384 (e.g. an ncore x nvirt block contracted over a long K).
+ * Computed by the FP64 FMA kernels of cvsadc_zgemm (FP64 precision) on
+ * cuda_stream (NULL: the legacy default stream); returns after that stream
+ * is synchronised.
+ *
+ * No allocation: the split-K partial products live in a fixed 8 MiB device
+ * array compiled into the library (every GPU that loads the library holds
+ * it until the process exits).  The first call on a device looks up that
+ * array's device address for the current device (cudaGetSymbolAddress) and
+ * sets a kernel attribute; it calls no cudaMalloc, cudaFree or allocating
+ * library routine.  All calls on a device share the array, so calls that
+ * overlap on the GPU (other streams or host threads) race on it: serialise
+ * them.  Each call writes every partial it reads, so nothing carries over.
+ * Errors: CVSADC_EINVAL for NULL pointers, non-positive sizes, a product
+ * beyond the limits above, or leading dimensions smaller than the rows;
+ * CVSADC_ECUDA for a CUDA error. */
+#define CVSADC_NOALLOC_MAX_MN 4096
+#define CVSADC_NOALLOC_MAX_M_PLUS_N 384
+int cvsadc_zgemm_small_noalloc(void* cuda_stream, int32_t M, int32_t N,
+                               int32_t K, const void* A, int64_t lda,
+                               const void* B, int64_t ldb, void* C,
+                               int64_t ldc);
+
 /* Davidson on the prepared problem (see cvsadc_solve for outputs). */
 int cvsadc_davidson(cvsadc_ctx* ctx, const cvsadc_params* params,
                     double* omega, void* X, double* osc, cvsadc_info* info);

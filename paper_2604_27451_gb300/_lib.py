@@ -78,6 +78,10 @@ _SIGNATURES = {
                                     ctypes.c_int32]),
     "cvsadc_davidson": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp,
                                        ctypes.POINTER(Info)]),
+    "cvsadc_zgemm_small_noalloc": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.c_int32, _vp, ctypes.c_int64,
+                                                  _vp, ctypes.c_int64, _vp,
+                                                  ctypes.c_int64]),
     "cvsadc_launch_count": (ctypes.c_int64, []),
     "cvsadc_kernel_timing": (None, [ctypes.c_int32]),
     "cvsadc_kernel_stats": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
