@@ -69,6 +69,21 @@ struct Split<6> {
   }
 };
 
+// CTA rasterisation: consecutive CTAs walk groups of RASTER M-tiles
+// column by column, so the CTAs resident at one time share A and B panels
+// in L2 instead of streaming the whole B operand once per M-tile row.
+constexpr int RASTER = 8;
+__device__ __forceinline__ void tile_coords(int& mt, int& nt) {
+  const int num_n = gridDim.x, num_m = gridDim.y;
+  const int pid = blockIdx.y * num_n + blockIdx.x;
+  const int per_group = RASTER * num_n;
+  const int first_m = (pid / per_group) * RASTER;
+  const int gsz = min(num_m - first_m, RASTER);
+  const int local = pid - (first_m / RASTER) * per_group;
+  mt = first_m + local % gsz;
+  nt = local / gsz;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -182,7 +197,9 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ int fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  int mt, nt;
+  tile_coords(mt, nt);
+  const int m0 = mt * BM, n0 = nt * BN;
   const int z = blockIdx.z;
   const int ktb = z * zkt, kte = min(nkt, ktb + zkt);  // non-empty by launch
 
@@ -567,7 +584,9 @@ __global__ void __launch_bounds__(576, 1)
   __shared__ int fail;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * SBN;
+  int mt, nt;
+  tile_coords(mt, nt);
+  const int m0 = mt * BM, n0 = nt * SBN;
   const int z = blockIdx.z;
   // this CTA's k-tiles of every pair: [zb, ze) relative to the pair start
   const int zb = z * zl, ze = min(ktpp, zb + zl);

@@ -185,8 +185,8 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
   // contractions with enough work per packed element
   // small outputs with a long K: all dot products at once, FP64
   const bool small = (int64_t)M * N <= 4096 && M + N <= 384 && K >= 4096;
-  const bool tc = !small && prec != CVSADC_FP64 && M >= 32 && N >= 16 &&
-                  K >= 64 && (double)M * N * K >= 1e7;
+  const bool tc = !small && prec != CVSADC_FP64 && M >= 32 && K >= 64 &&
+                  (double)M * N * K >= 1e7;
   if (tc) {
     CVS_REQUIRE(tc_available(), CVSADC_EINVAL,
                 "tensor-core precisions need an sm_103 GPU with tcgen05");
@@ -420,12 +420,14 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g) {
   const View s1rows = rows2(view(sig, 0, 1), N, v, nc);
   gemm(c, prec, g * nc, v, (int)vL, -1.0, view(S, vL, 1),
        rows2(view(B + (int64_t)o * n + o, 0, n), 1, nn, L), 0.0, s1rows);
-  const View s1cols = cols2(view(sig, v, 0), N, 1, v);  // (K, (q,c))
-  gemm(c, prec, nc, g * v, nc * L, 1.0, cols2(view(B, 1, 0), n, nn, L),
-       cols2(rows2(view(S, 0, 0), vL, 1, L), N1L, L, v), 1.0, s1cols);
-  gemm(c, prec, nc, g * v, nw * L, -1.0,
-       cols2(view(B + (int64_t)nc * n, 1, 0), n, nn, L),
-       cols2(view(R, 1, 0), wvL, (int64_t)nw * L, v), 1.0, s1cols);
+  // the two contractions with the core index K as output column: rows
+  // (q, c) so that the long dimension is the GEMM's M
+  const View s1t = rows2(view(sig, 0, v), N, 1, v);  // ((q,c), K)
+  gemm(c, prec, g * v, nc, nc * L, 1.0,
+       cols2(rows2(view(S, 0, 0), N1L, L, v), vL, 1, L),
+       rows2(view(B, 0, 1), n, nn, L), 1.0, s1t);
+  gemm(c, prec, g * v, nc, nw * L, -1.0, view(R, (int64_t)nw * L, 1),
+       rows2(view(B + (int64_t)nc * n, 0, 1), n, nn, L), 1.0, s1t);
   // Y[(q,I,a)][P] = sum_c x_Ic B^P_ac - sum_K x_Ka B^P_KI
   gemm(c, prec, g * nc, (int)vL, v, 1.0, rows2(view(x, 0, 1), N, v, nc),
        cols2(view(B + (int64_t)o * n + o, 1, 0), n, nn, L), 0.0,
