@@ -101,8 +101,8 @@ typedef struct {
                              iterations after the mixed Davidson (which stops
                              at max(conv_residual, 3e-4) for BF16X3 and
                              max(conv_residual, 1e-6) for SLICE4); each
-                             costs one FP64 sigma per unconverged root;
-                             default 2 */
+                             costs one FP64-class sigma per unconverged
+                             root; default 20 (stops when converged) */
 } cvsadc_params;
 
 typedef struct {

@@ -923,7 +923,7 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
     X0.ensure((size_t)k * c->N * sizeof(cplx));
     CVS_CUDA(cudaMemcpyAsync(X0.p, Xd.p, (size_t)k * c->N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, c->stream));
-    int sweeps = p->refine_sweeps > 0 ? p->refine_sweeps : 2;
+    int sweeps = p->refine_sweeps > 0 ? p->refine_sweeps : 20;
     const int rprec = refine_precision(p->precision);
     DavResult r2 = davidson_impl(c, rprec, k, sweeps, max_sub, tol, X0.c(), k,
                                  Xd.c(), w.data());
