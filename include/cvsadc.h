@@ -39,6 +39,9 @@
  *   (outputs then hold the best estimate).  No exception crosses the ABI.
  * Threads/streams: one context per host thread; all work is issued on the
  *   context's stream and every call returns after that stream is synchronised.
+ *   Device inputs are read on the context's stream with no wait on any other
+ *   stream: the caller makes them ready first (a non-blocking context stream
+ *   is not ordered after work still running on another stream).
  * Units: Hartree.
  */
 #ifndef CVSADC_H
@@ -155,6 +158,29 @@ const char* cvsadc_last_error(cvsadc_ctx* ctx);
 int cvsadc_solve(cvsadc_ctx* ctx, const cvsadc_params* params,
                  const double* eps, const void* B, const void* dip,
                  double* omega, void* X, double* osc, cvsadc_info* info);
+
+/* --------------------------------------------------------------------
+ * cvsadc_grad -- gradient of E = sum of the selected lowest roots.
+ * Because M is Hermitian and the eigenvectors are normalised, dE/dtheta =
+ * sum_n x_n^H (dM/dtheta) x_n (Hellmann-Feynman); the library builds the
+ * problem in FP64 (no dipoles, no FNS: tau must be <= 0), finds the roots
+ * with the sigma of params->precision (the tensor-core precisions followed
+ * by the FP64-class refinement, as in cvsadc_solve), then runs an FP64
+ * adjoint pass through every contraction of M -- the M11 pieces, the MP2
+ * amplitudes t2 (with their energy denominators, from the stored <ab||ij>)
+ * and the B^P couplings.
+ *   root_mask : [nroots] 0/1 (NULL: all roots) -- which roots are summed
+ *   omega     : [nroots] out, the roots
+ *   grad_eps  : [n] out, dE/deps
+ *   grad_B    : [naux][n][n] complex out, dE/dRe B + i dE/dIm B, projected on
+ *               Hermitian matrices (each B^P is constrained Hermitian); for a
+ *               Hermitian perturbation dB, dE = Re sum conj(grad_B) dB.
+ * Memory space per params->flags.  Errors: EINVAL (tau > 0, bad mask),
+ * ENOTCONV (Davidson did not converge to conv_residual, default 1e-8),
+ * ENOMEM, ECUDA. */
+int cvsadc_grad(cvsadc_ctx* ctx, const cvsadc_params* params,
+                const double* eps, const void* B, const int32_t* root_mask,
+                double* omega, double* grad_eps, void* grad_B);
 
 /* --------------------------------------------------------------------
  * Stage entry points.  cvsadc_prepare runs everything before the

@@ -46,6 +46,16 @@ def _ptr(x):
     return ctypes.c_void_p(x.ctypes.data), False
 
 
+def _inputs_ready(*xs):
+    """The library reads device inputs on its own stream without waiting on
+    torch's: finish the work torch has queued on the producing stream."""
+    for x in xs:
+        if _is_torch_cuda(x):
+            import torch
+            torch.cuda.current_stream(x.device).synchronize()
+            return
+
+
 class Context:
     """One libcvsadc context (one device, one stream)."""
 
@@ -98,6 +108,7 @@ class Context:
     def prepare(self, eps, B, dip=None, ncore=None, nval=None, nvirt=None,
                 precision="fp64", tau=0.0):
         naux = B.shape[0]
+        _inputs_ready(eps, B, dip)
         pe, dev = _ptr(eps)
         pb, _ = _ptr(B)
         pd, _ = _ptr(dip)
@@ -152,6 +163,7 @@ class Context:
         """sigma = M x for x [nvec][N] (numpy host or torch CUDA)."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else precision
         nvec = x.shape[0] if x.ndim == 2 else 1
+        _inputs_ready(x)
         px, dev = _ptr(x)
         if out is None:
             if dev:
@@ -170,6 +182,7 @@ class Context:
         M, K = A.shape
         K2, N = B.shape
         assert K == K2
+        _inputs_ready(A, B)
         pa, dev = _ptr(A)
         pb, _ = _ptr(B)
         if dev:
@@ -201,11 +214,39 @@ class Context:
         self._check(rc, allow_notconv=True)
         return dict(omega=omega, osc=osc, X=X, info=info.as_dict(), status=rc)
 
+    def grad(self, eps, B, ncore, nval, nvirt, nroots, root_mask=None, conv=1e-8,
+             max_iter=0, precision="fp64"):
+        """(roots, dE/deps, dE/dB) for E = sum of the selected roots, through
+        cvsadc_grad (FP64 problem, root solve in `precision` with FP64-class
+        refinement, FP64 adjoint pass).  Host numpy or torch CUDA."""
+        naux = B.shape[0]
+        _inputs_ready(eps, B)
+        pe, dev = _ptr(eps)
+        pb, _ = _ptr(B)
+        p = self.params(ncore, nval, nvirt, naux, nroots, precision, 0.0, conv,
+                        max_iter, 0, CVSADC_FLAG_DEVICE_PTRS if dev else 0)
+        mask = None if root_mask is None else np.ascontiguousarray(root_mask, dtype=np.int32)
+        if dev:
+            import torch
+            omega = torch.empty(nroots, dtype=torch.float64, device=eps.device)
+            ge = torch.empty_like(eps)
+            gB = torch.empty_like(B)
+        else:
+            omega = np.empty(nroots)
+            ge = np.empty_like(eps)
+            gB = np.empty_like(B)
+        rc = self.lib.cvsadc_grad(self.h, ctypes.byref(p), pe, pb,
+                                  ctypes.c_void_p(mask.ctypes.data) if mask is not None else None,
+                                  _ptr(omega)[0], _ptr(ge)[0], _ptr(gB)[0])
+        self._check(rc)
+        return omega, ge, gB
+
     def solve(self, eps, B, dip, ncore, nval, nvirt, nroots, precision="fp64",
               tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, return_x=False,
               refine=True, refine_sweeps=0):
         """The whole path through cvsadc_solve."""
         naux = B.shape[0]
+        _inputs_ready(eps, B, dip)
         pe, dev = _ptr(eps)
         pb, _ = _ptr(B)
         pd, _ = _ptr(dip)
@@ -245,3 +286,25 @@ class Context:
             X = X[: nroots * self._shape["N"]].reshape(nroots, self._shape["N"])
         return dict(omega=omega, osc=osc if dip is not None else None, X=X,
                     info=info.as_dict(), status=rc)
+
+
+def energy_function(ctx, ncore, nval, nvirt, nroots, precision="fp64", conv=1e-8):
+    """A torch.autograd.Function: E(eps, B) = sum of the lowest nroots
+    CVS-ADC(2) roots, with the gradient from the library's adjoint pass
+    (cvsadc_grad).  eps and B are torch CUDA tensors (B complex128)."""
+    import torch
+
+    class CVSADCEnergy(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, eps, B):
+            omega, ge, gB = ctx.grad(eps.contiguous(), B.contiguous(), ncore, nval,
+                                     nvirt, nroots, conv=conv, precision=precision)
+            fctx.save_for_backward(ge, gB)
+            return omega.sum()
+
+        @staticmethod
+        def backward(fctx, gE):
+            ge, gB = fctx.saved_tensors
+            return gE * ge, gE * gB
+
+    return CVSADCEnergy

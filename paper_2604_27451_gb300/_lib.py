@@ -65,6 +65,8 @@ _SIGNATURES = {
     "cvsadc_last_error": (ctypes.c_char_p, [_vp]),
     "cvsadc_solve": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp,
                                     _vp, _vp, _vp, ctypes.POINTER(Info)]),
+    "cvsadc_grad": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp,
+                                   _vp]),
     "cvsadc_prepare": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp,
                                       ctypes.POINTER(Info)]),
     "cvsadc_prepared_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32),

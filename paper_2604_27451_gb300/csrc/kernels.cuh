@@ -125,6 +125,23 @@ void scale_rows(cudaStream_t s, cplx* X, int rows, int cols, int ld,
 // one-time kernel attribute setup for the current device
 void init_kernel_attributes();
 
+// ------------------------------------------------------------ adjoint
+// backward of the M11 assembly from rho[s][t] = sum_n conj(x_s) x_t
+void m11_backward(cudaStream_t s, const cplx* rho, int nc, int nv, int o,
+                  cplx* gC1, cplx* gC2, cplx* gX, cplx* gY, cplx* gZ,
+                  double* gE);
+// gg2 <- gg2 + gt2 / D (in place) and the denominators' share of gE
+void t2_backward(cudaStream_t s, const cplx* gt2, cplx* gg2, const cplx* g2,
+                 int o, int v, const double* eps, double* gE);
+// gQ band [(al,i),(b,j)] from gR [i][j][a][b]
+void q_backward_band(cudaStream_t s, const cplx* gR, int a0, int na, int o,
+                     int v, cplx* gQ);
+// M22's share of gE from k packed vectors X [k][N]
+void m22_backward(cudaStream_t s, const cplx* X, int k, int64_t N, int64_t N1,
+                  int nc, int nw, int nv, double* gE);
+// G^P <- (G^P + G^P^H)/2 for nmat n x n matrices
+void herm_project(cudaStream_t s, cplx* G, int n, int64_t nmat);
+
 // ---------------------------------------------------- Jacobi (FP64)
 // Hermitian eigensolver: A [n][n] row-major (destroyed), eigenvalues w
 // ascending, eigenvectors as columns of Vec [n][n].  One CTA, cyclic

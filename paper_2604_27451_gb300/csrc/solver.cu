@@ -892,6 +892,37 @@ double mixed_tolerance(int prec) {
   return prec == CVSADC_MIXED_BF16X3 ? 3e-4 : 1e-6;
 }
 
+// Lowest k roots of the prepared problem into Xd [k][N] and w: Davidson in
+// `prec`, then, for the tensor-core precisions (unless no_refine), a
+// continuation with FP64-class sigma from the converged Ritz vectors, each
+// sweep costing one sigma per unconverged root.  t_refine gets the time of
+// the second phase.
+DavResult solve_roots(cvsadc_ctx* c, int prec, int k, double tol, int max_iter,
+                      int max_sub, int refine_sweeps, bool no_refine, cplx* Xd,
+                      double* w, double* t_refine) {
+  const bool refine = needs_refine(prec) && !no_refine;
+  const double tol_phase = refine ? std::max(tol, mixed_tolerance(prec)) : tol;
+  DavResult r = davidson_impl(c, prec, k, max_iter, max_sub, tol_phase, nullptr,
+                              0, Xd, w, needs_refine(prec));
+  const double t1 = now_ms();
+  if (refine) {
+    DBuf X0;
+    X0.ensure((size_t)k * c->N * sizeof(cplx));
+    CVS_CUDA(cudaMemcpyAsync(X0.p, Xd, (size_t)k * c->N * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, c->stream));
+    const int sweeps = refine_sweeps > 0 ? refine_sweeps : 20;
+    DavResult r2 = davidson_impl(c, refine_precision(prec), k, sweeps, max_sub,
+                                 tol, X0.c(), k, Xd, w);
+    r.iters += r2.iters;
+    r.sigmas += r2.sigmas;
+    r.t_sigma_ms += r2.t_sigma_ms;
+    r.converged = r2.converged;
+    r.maxres = r2.maxres;
+  }
+  if (t_refine) *t_refine = refine ? now_ms() - t1 : 0.0;
+  return r;
+}
+
 void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
                     void* X, double* osc, cvsadc_info* info) {
   CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
@@ -907,33 +938,12 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
   DBuf Xd;
   Xd.ensure((size_t)k * c->N * sizeof(cplx));
   std::vector<double> w(k);
-  double tol_phase = tol;
-  if (needs_refine(p->precision) && !(p->flags & CVSADC_FLAG_NO_REFINE))
-    tol_phase = std::max(tol, mixed_tolerance(p->precision));
-  DavResult r = davidson_impl(c, p->precision, k, max_iter, max_sub, tol_phase,
-                              nullptr, 0, Xd.c(), w.data(),
-                              needs_refine(p->precision));
-  double t1 = now_ms();
   double t_ref = 0;
-  if (needs_refine(p->precision) && !(p->flags & CVSADC_FLAG_NO_REFINE)) {
-    // FP64 residual correction: from the converged mixed-precision Ritz
-    // vectors, sigma in FP64, Rayleigh-Ritz, and correction steps, each
-    // costing one FP64 sigma per unconverged root
-    DBuf X0;
-    X0.ensure((size_t)k * c->N * sizeof(cplx));
-    CVS_CUDA(cudaMemcpyAsync(X0.p, Xd.p, (size_t)k * c->N * sizeof(cplx),
-                             cudaMemcpyDeviceToDevice, c->stream));
-    int sweeps = p->refine_sweeps > 0 ? p->refine_sweeps : 20;
-    const int rprec = refine_precision(p->precision);
-    DavResult r2 = davidson_impl(c, rprec, k, sweeps, max_sub, tol, X0.c(), k,
-                                 Xd.c(), w.data());
-    r.iters += r2.iters;
-    r.sigmas += r2.sigmas;
-    r.t_sigma_ms += r2.t_sigma_ms;
-    r.converged = r2.converged;
-    r.maxres = r2.maxres;
-    t_ref = now_ms() - t1;
-  }
+  DavResult r = solve_roots(c, p->precision, k, tol, max_iter, max_sub,
+                            p->refine_sweeps,
+                            (p->flags & CVSADC_FLAG_NO_REFINE) != 0, Xd.c(),
+                            w.data(), &t_ref);
+  double t1 = now_ms() - t_ref;
   phase_fix(c->stream, Xd.c(), k, c->N, c->dv_misc.d());
   if (dev)
     CVS_CUDA(cudaMemcpyAsync(omega, w.data(), k * sizeof(double),
@@ -993,6 +1003,242 @@ void check_device_error(cvsadc_ctx* c) {
     snprintf(b, sizeof b, "a bounded device wait expired (code %d)", e);
     throw Error{CVSADC_ETIMEOUT, b};
   }
+}
+
+
+// ===================================================================== S10
+// Gradient of E = sum of selected roots with respect to the spinor energies
+// and the Cholesky vectors.  M is Hermitian and the eigenvectors are
+// normalised, so dE/dtheta = sum_n x_n^H (dM/dtheta) x_n (Hellmann-Feynman)
+// with the x_n held fixed: the reverse pass below differentiates
+//   f = sum_n [x1^H M11 x1 + 2 Re x2^H M21 x1 + x2^H M22 x2]
+// through every forward contraction (M11 pieces, t2 and its energy
+// denominators, the B^P couplings).  Complex gradients follow
+// g_z = df/dRe z + i df/dIm z; grad_B is projected on Hermitian matrices
+// (the inputs' manifold).
+
+// a view with the same geometry into the gradient of the tensor it reads
+View mirror(const View& v, const cplx* base, cplx* gbase) {
+  View g = v;
+  g.p = gbase + (v.p - base);
+  g.conj = 0;
+  g.ext = -1;
+  return g;
+}
+
+// backward of C = alpha * A B: gradients into the tensors A and B read
+// (either may be skipped with a null mirror); gC is C's gradient view.
+void gemm_backward(cvsadc_ctx* c, int M, int N, int K, double alpha, View A,
+                   View gA, View B, View gB, View gC) {
+  if (gA.p) {
+    // d/dA: gC B^H (A read plain) or conj(gC) B^T (A read conjugated)
+    View Bh = A.conj ? trans(B) : conj_of(trans(B));
+    View g = A.conj ? conj_of(gC) : gC;
+    gemm64(c, M, K, N, alpha, g, Bh, 1.0, gA);
+  }
+  if (gB.p) {
+    View Ah = B.conj ? trans(A) : conj_of(trans(A));
+    View g = B.conj ? conj_of(gC) : gC;
+    gemm64(c, K, N, M, alpha, Ah, g, 1.0, gB);
+  }
+}
+
+void grad_impl(cvsadc_ctx* c, const cplx* X, int k, double* gE, cplx* gB) {
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
+            L = c->naux;
+  const int64_t nn = (int64_t)n * n, N1 = c->N1, N = c->N, vv = (int64_t)v * v,
+                ovv = (int64_t)o * vv, vo = (int64_t)v * o;
+  const cplx* B = c->B.c();
+  const cplx* t2 = c->t2.c();
+  const cplx* g2 = c->g2.c();
+  cudaStream_t s = c->stream;
+  CVS_CUDA(cudaMemsetAsync(gE, 0, n * sizeof(double), s));
+  CVS_CUDA(cudaMemsetAsync(gB, 0, (size_t)L * nn * sizeof(cplx), s));
+  auto mB = [&](const View& vw) { return mirror(vw, B, gB); };
+
+  // ---------------------------------------------------- M11 (singles)
+  DBuf rho, gC1, gC2, gX, gY, gZ, gt2, gg2;
+  rho.ensure(N1 * N1 * sizeof(cplx));
+  // rho[s][t] = sum_q conj(x_s) x_t
+  gemm64(c, (int)N1, (int)N1, k, 1.0, conj_of(view(X, 1, N)), view(X, N, 1), 0.0,
+         view(rho.p, N1, 1));
+  gC1.ensure(vv * nc * nc * sizeof(cplx));
+  gC2.ensure(N1 * N1 * sizeof(cplx));
+  gZ.ensure(N1 * N1 * sizeof(cplx));
+  gX.ensure(vv * sizeof(cplx));
+  gY.ensure((size_t)nc * nc * sizeof(cplx));
+  m11_backward(s, rho.c(), nc, v, o, gC1.c(), gC2.c(), gX.c(), gY.c(), gZ.c(), gE);
+  // C1[(a,b),(J,I)] = (ab|JI)
+  {
+    View A = rows2(view(B + (int64_t)o * n + o, 0, nn), n, 1, v);
+    View Bv = cols2(view(B, nn, 0), n, 1, nc);
+    gemm_backward(c, v * v, nc * nc, L, 1.0, A, mB(A), Bv, mB(Bv),
+                  view(gC1.p, nc * nc, 1));
+  }
+  // C2[(I,a),(J,b)] = (aI|Jb)
+  {
+    View A = rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v);
+    View Bv = cols2(view(B + o, nn, 0), n, 1, v);
+    gemm_backward(c, (int)N1, (int)N1, L, 1.0, A, mB(A), Bv, mB(Bv),
+                  view(gC2.p, N1, 1));
+  }
+  // X, Y, Z through t2 and <ab||ij>
+  gt2.ensure((size_t)o * ovv * sizeof(cplx));
+  gg2.ensure((size_t)o * ovv * sizeof(cplx));
+  CVS_CUDA(cudaMemsetAsync(gt2.p, 0, (size_t)o * ovv * sizeof(cplx), s));
+  CVS_CUDA(cudaMemsetAsync(gg2.p, 0, (size_t)o * ovv * sizeof(cplx), s));
+  auto mT = [&](const View& vw) { return mirror(vw, t2, gt2.c()); };
+  auto mG = [&](const View& vw) { return mirror(vw, g2, gg2.c()); };
+  {
+    View A = cols2(view(t2, v, 0), vv, 1, v);
+    View Bv = conj_of(rows2(view(g2, 0, v), vv, 1, v));
+    gemm_backward(c, v, v, o * o * v, 1.0, A, mT(A), Bv, mG(Bv), view(gX.p, v, 1));
+  }
+  {
+    View A = view(t2, ovv, 1);
+    View Bv = conj_of(view(g2, 1, ovv));
+    gemm_backward(c, nc, nc, (int)ovv, 1.0, A, mT(A), Bv, mG(Bv), view(gY.p, nc, 1));
+  }
+  {
+    View A = cols2(rows2(view(t2, 0, 0), ovv, v, v), vv, 1, v);
+    View Bv = conj_of(cols2(rows2(view(g2, 0, 0), vv, 1, v), ovv, v, v));
+    gemm_backward(c, (int)N1, (int)N1, o * v, 1.0, A, mT(A), Bv, mG(Bv),
+                  view(gZ.p, N1, 1));
+  }
+  rho.release();
+  gC1.release();
+  gC2.release();
+  gZ.release();
+  // t2 = g/D, g = (ai|bj) - (aj|bi): gR in gg2
+  t2_backward(s, gt2.c(), gg2.c(), g2, o, v, c->eps.d(), gE);
+  gt2.release();
+  {
+    int64_t per_a = (int64_t)o * vo * sizeof(cplx);
+    int na = (int)std::max<int64_t>(1, std::min<int64_t>(v, (2LL << 30) / per_a));
+    DBuf gQ;
+    gQ.ensure((size_t)na * per_a);
+    for (int a0 = 0; a0 < v; a0 += na) {
+      const int nb = std::min(na, v - a0);
+      q_backward_band(s, gg2.c(), a0, nb, o, v, gQ.c());
+      View A = rows2(view(B + (int64_t)(o + a0) * n, 0, nn), n, 1, o);
+      View Bv = cols2(view(B + (int64_t)o * n, nn, 0), n, 1, o);
+      gemm_backward(c, nb * o, (int)vo, L, 1.0, A, mB(A), Bv, mB(Bv),
+                    view(gQ.p, vo, 1));
+    }
+  }
+  gg2.release();
+
+  // --------------------------------------------- couplings, by root groups
+  const int64_t wv = (int64_t)nw * v, vL = (int64_t)v * L, wvL = wv * L;
+  const int64_t N1L = N1 * L, N1wv = N1 * wv;
+  const double per_vec = (3.0 * N1wv + 2.0 * N1L + 2.0 * wvL) * sizeof(cplx);
+  const int gmax = (int)std::max(1.0, std::min((double)k, 32e9 / per_vec));
+  DBuf Yt, Yb, Vv, gY2, gV2;
+  for (int q0 = 0; q0 < k; q0 += gmax) {
+    const int g = std::min(gmax, k - q0);
+    const cplx* x = X + (int64_t)q0 * N;
+    Yt.ensure((size_t)g * N1wv * sizeof(cplx));
+    Yb.ensure((size_t)g * N1L * sizeof(cplx));
+    Vv.ensure((size_t)g * wvL * sizeof(cplx));
+    gY2.ensure((size_t)g * N1L * sizeof(cplx));
+    gV2.ensure((size_t)g * wvL * sizeof(cplx));
+    for (int q = 0; q < g; ++q)
+      unpack_doubles(s, x + q * N + N1, nc, nw, v, Yt.c() + q * N1wv);
+    // forward intermediates Y and Vv (as in sigma)
+    View A1 = rows2(view(x, 0, 1), N, v, nc);
+    View B1 = cols2(view(B + (int64_t)o * n + o, 1, 0), n, nn, L);
+    gemm64(c, g * nc, (int)vL, v, 1.0, A1, B1, 0.0, view(Yb.p, vL, 1));
+    View A2 = rows2(view(x, 0, v), N, 1, v);
+    View B2 = cols2(view(B, n, 0), 1, nn, L);
+    View CY2 = cols2(rows2(view(Yb.p, 0, 0), N1L, L, v), vL, 1, L);
+    gemm64(c, g * v, nc * L, nc, -1.0, A2, B2, 1.0, CY2);
+    View B3 = cols2(view(B + nc, n, 0), 1, nn, L);
+    View CV = cols2(rows2(view(Vv.p, 0, 0), wvL, L, v), vL, 1, L);
+    gemm64(c, g * v, nw * L, nc, 1.0, A2, B3, 0.0, CV);
+    // f_coup = Re(-2 sum conj(y) G) -> gG = -2 y (the unpacked doubles)
+    View gG1 = view(Yt.p, wv, 1);
+    View gG2 = cols2(view(Yt.p, wv, 0), N1wv, 1, (int)wv);
+    // G1 = Y B4: gY = gG B4^H, gB(B4) += Y^H gG
+    View B4 = cols2(view(B + (int64_t)o * n + nc, nn, 0), 1, n, v);
+    gemm64(c, (int)(g * N1), L, (int)wv, -2.0, gG1, conj_of(trans(B4)), 0.0,
+           view(gY2.p, L, 1));
+    gemm64(c, L, (int)wv, (int)(g * N1), -2.0, conj_of(trans(view(Yb.p, L, 1))),
+           gG1, 1.0, mB(B4));
+    // G2 = -A5 Vv: gB(A5) += -gG Vv^H, gVv = -A5^H gG
+    View A5 = rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v);
+    gemm64(c, (int)N1, L, (int)(g * wv), 2.0, gG2, conj_of(trans(view(Vv.p, 1, L))),
+           1.0, mB(A5));
+    gemm64(c, L, (int)(g * wv), (int)N1, 2.0, conj_of(trans(A5)), gG2, 0.0,
+           view(gV2.p, 1, L));
+    // Vv = A2 B3: gB(B3) += A2^H gVv
+    View gCV = cols2(rows2(view(gV2.p, 0, 0), wvL, L, v), vL, 1, L);
+    gemm64(c, nc, nw * L, g * v, 1.0, conj_of(trans(A2)), gCV, 1.0, mB(B3));
+    // Y = A1 B1 - A2 B2: gB(B1) += A1^H gY, gB(B2) -= A2^H gY
+    gemm64(c, v, (int)vL, g * nc, 1.0, conj_of(trans(A1)), view(gY2.p, vL, 1), 1.0,
+           mB(B1));
+    View gCY2 = cols2(rows2(view(gY2.p, 0, 0), N1L, L, v), vL, 1, L);
+    gemm64(c, nc, nc * L, g * v, -1.0, conj_of(trans(A2)), gCY2, 1.0, mB(B2));
+  }
+  // M22
+  m22_backward(s, X, k, N, N1, nc, nw, v, gE);
+  herm_project(s, gB, n, L);
+  c->sync();
+}
+
+void grad_entry(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
+                const void* B, const int32_t* root_mask, double* omega,
+                double* grad_eps, void* grad_B) {
+  CVS_REQUIRE(p && eps && B && omega && grad_eps && grad_B, CVSADC_EINVAL,
+              "NULL argument");
+  CVS_REQUIRE(p->fns_threshold <= 0, CVSADC_EINVAL,
+              "gradients are defined for the untruncated virtual space (tau <= 0)");
+  CVS_REQUIRE(p->precision >= CVSADC_FP64 && p->precision <= CVSADC_FP64_SLICE7,
+              CVSADC_EINVAL, "bad precision");
+  // the problem (t2, M11) is always built in FP64, so that the eigenpairs
+  // and the adjoint below belong to the same matrix; params->precision only
+  // selects the sigma of the Davidson phase, which for the tensor-core
+  // precisions is followed by the FP64-class refinement
+  cvsadc_params q = *p;
+  q.precision = CVSADC_FP64;
+  q.flags = (p->flags & CVSADC_FLAG_DEVICE_PTRS);
+  prepare_impl(c, &q, eps, B, nullptr, nullptr);
+  const int k = q.nroots;
+  CVS_REQUIRE(k >= 1 && k <= 64 && k <= c->N, CVSADC_EINVAL, "bad nroots");
+  const double tol = p->conv_residual > 0 ? p->conv_residual : 1e-8;
+  const int max_iter = p->max_iter > 0 ? p->max_iter : 400;
+  const int max_sub = std::min(p->max_subspace > 0 ? p->max_subspace : std::max(8 * k, 48), 128);
+  DBuf Xd;
+  Xd.ensure((size_t)k * c->N * sizeof(cplx));
+  std::vector<double> w(k);
+  // the gradient needs converged eigenvectors, so the refinement may run
+  // as long as the first phase
+  DavResult r = solve_roots(c, p->precision, k, tol, max_iter, max_sub,
+                            p->refine_sweeps > 0 ? p->refine_sweeps : max_iter,
+                            false, Xd.c(), w.data(), nullptr);
+  CVS_REQUIRE(r.converged == k, CVSADC_ENOTCONV, "Davidson did not converge");
+  // selected roots, contiguous
+  std::vector<int> sel;
+  for (int i = 0; i < k; ++i)
+    if (!root_mask || root_mask[i]) sel.push_back(i);
+  CVS_REQUIRE(!sel.empty(), CVSADC_EINVAL, "root_mask selects no root");
+  for (size_t i = 0; i < sel.size(); ++i)
+    if (sel[i] != (int)i)
+      CVS_CUDA(cudaMemcpyAsync(Xd.c() + i * c->N, Xd.c() + sel[i] * c->N,
+                               c->N * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                               c->stream));
+  DBuf gE, gBd;
+  gE.ensure(c->n * sizeof(double));
+  gBd.ensure((size_t)c->naux * c->n * c->n * sizeof(cplx));
+  grad_impl(c, Xd.c(), (int)sel.size(), gE.d(), gBd.c());
+  const bool dev = (p->flags & CVSADC_FLAG_DEVICE_PTRS) != 0;
+  download(c, grad_eps, gE.p, c->n * sizeof(double), dev);
+  download(c, grad_B, gBd.p, (size_t)c->naux * c->n * c->n * sizeof(cplx), dev);
+  if (dev)
+    CVS_CUDA(cudaMemcpyAsync(omega, w.data(), k * sizeof(double),
+                             cudaMemcpyHostToDevice, c->stream));
+  else
+    std::memcpy(omega, w.data(), k * sizeof(double));
+  c->sync();
 }
 
 template <typename F>
@@ -1228,6 +1474,15 @@ int cvsadc_davidson(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
                     void* X, double* osc, cvsadc_info* info) {
   if (!c || !p) return CVSADC_EINVAL;
   return guarded(c, [&] { davidson_entry(c, p, omega, X, osc, info); });
+}
+
+int cvsadc_grad(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
+                const void* B, const int32_t* root_mask, double* omega,
+                double* grad_eps, void* grad_B) {
+  if (!c || !p) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    grad_entry(c, p, eps, B, root_mask, omega, grad_eps, grad_B);
+  });
 }
 
 int cvsadc_solve(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,

@@ -362,3 +362,32 @@ def test_oscillator_linearity_and_phase():
     assert np.allclose(adc2.oscillator_strengths(w, X, F2), 6.25 * f, rtol=1e-13)
     ph = np.exp(1j * np.array([0.3, -1.2, 2.0]))[:, None]
     assert np.allclose(adc2.oscillator_strengths(w, X * ph, F), f, rtol=1e-13)
+
+
+# ------------------------------------------------- T10 reference gradient
+
+@pytest.mark.parametrize("shape,nroots", [((2, 2, 5, 6), 3), ((2, 4, 6, 9), 4)])
+def test_reference_gradient_matches_finite_differences(shape, nroots):
+    from oracle.grad import energy_gradient
+
+    nc, nw, nv, L = shape
+    inst = make_instance(nc, nw, nv, L, seed=7, scale=0.2)
+    w, ge, gB = energy_gradient(inst.eps, inst.B, nc, nw, nv, nroots)
+    rng = np.random.default_rng(1)
+
+    def E(eps, B):
+        return np.linalg.eigvalsh(adc2.adc_matrix(eps, B, nc, nw, nv))[:nroots].sum()
+
+    assert abs(E(inst.eps, inst.B) - w.sum()) < 1e-11
+    h = 1e-5
+    for _ in range(2):
+        d = rng.standard_normal(inst.B.shape) + 1j * rng.standard_normal(inst.B.shape)
+        d = 0.5 * (d + np.conj(d.transpose(0, 2, 1)))
+        fd = (E(inst.eps, inst.B + h * d) - E(inst.eps, inst.B - h * d)) / (2 * h)
+        ad = np.real(np.sum(np.conj(gB) * d))
+        assert abs(fd - ad) < 1e-7 * max(1.0, abs(ad)), (fd, ad)
+        de = rng.standard_normal(inst.eps.shape)
+        fd = (E(inst.eps + h * de, inst.B) - E(inst.eps - h * de, inst.B)) / (2 * h)
+        assert abs(fd - np.sum(ge * de)) < 1e-7 * max(1.0, abs(fd))
+    # the projected gradient is Hermitian
+    assert np.abs(gB - np.conj(gB.transpose(0, 2, 1))).max() < 1e-14
