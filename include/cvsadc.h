@@ -271,8 +271,9 @@ void cvsadc_kernel_stats_reset(void);
  * array compiled into the library (every GPU that loads the library holds
  * it until the process exits).  The first call on a device looks up that
  * array's device address for the current device (cudaGetSymbolAddress) and
- * sets a kernel attribute; it calls no cudaMalloc, cudaFree or allocating
- * library routine.  All calls on a device share the array, so calls that
+ * sets a kernel attribute, so make that first call on each device before
+ * any stream capture begins; no call makes a cudaMalloc, cudaFree or
+ * allocating library routine.  All calls on a device share the array, so calls that
  * overlap on the GPU (other streams or host threads) race on it: serialise
  * them.  Each call writes every partial it reads, so nothing carries over.
  * Errors: CVSADC_EINVAL for NULL pointers, non-positive sizes, a product

@@ -35,7 +35,9 @@ std::map<int, cplx*> g_na_addr;  // device -> address of the array there
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name is only a host-side stand-in, so the address comes from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  This
+// set-up runs inside the first call on each device, which should therefore
+// come before any stream capture begins.
 cplx* noalloc_scratch(int dev) {
   std::lock_guard<std::mutex> l(g_na_mu);
   auto it = g_na_addr.find(dev);
