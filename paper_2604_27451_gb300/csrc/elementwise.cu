@@ -540,27 +540,32 @@ __global__ void absmax_kernel(const cplx* x, int64_t N, double* pv,
   }
 }
 
-__global__ void phase_apply_kernel(cplx* x, int64_t N, const double* pv,
-                                   const int64_t* pi, int nb) {
-  const int r = blockIdx.y;
-  __shared__ cplx ph;
-  if (threadIdx.x == 0) {
-    double best = -1.0;
-    int64_t bi = 0;
-    for (int b = 0; b < nb; ++b) {
-      double v = pv[r * nb + b];
-      int64_t i = pi[r * nb + b];
-      if (v > best || (v == best && i < bi)) {
-        best = v;
-        bi = i;
-      }
+// per vector: the unit phase that makes its largest-modulus entry real and
+// positive, from the block partials of absmax_kernel.  It runs as its own
+// launch, before any entry is rotated: a phase computed inside the rotating
+// kernel would read a pivot that another block may already have rotated.
+__global__ void phase_pick_kernel(const cplx* x, int64_t N, const double* pv,
+                                  const int64_t* pi, int nb, cplx* ph) {
+  const int r = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  double best = -1.0;
+  int64_t bi = 0;
+  for (int b = 0; b < nb; ++b) {
+    double v = pv[r * nb + b];
+    int64_t i = pi[r * nb + b];
+    if (v > best || (v == best && i < bi)) {
+      best = v;
+      bi = i;
     }
-    cplx v = x[(int64_t)r * N + bi];
-    double m = hypot(v.x, v.y);
-    ph = m > 0 ? cmake(v.x / m, -v.y / m) : cmake(1, 0);
   }
-  __syncthreads();
-  cplx p = ph;
+  cplx v = x[(int64_t)r * N + bi];
+  double m = hypot(v.x, v.y);
+  ph[r] = m > 0 ? cmake(v.x / m, -v.y / m) : cmake(1, 0);
+}
+
+__global__ void phase_apply_kernel(cplx* x, int64_t N, const cplx* ph) {
+  const int r = blockIdx.y;
+  const cplx p = ph[r];
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
        n += (int64_t)gridDim.x * blockDim.x)
     x[(int64_t)r * N + n] = cmul(x[(int64_t)r * N + n], p);
@@ -822,10 +827,13 @@ void phase_fix(cudaStream_t s, cplx* x, int k, int64_t N, double* work) {
   const int nb = 152;
   double* pv = work;
   int64_t* pi = (int64_t*)(work + (size_t)nb * k);
+  cplx* ph = (cplx*)(pi + (size_t)nb * k);
   dim3 grid(nb, k);
   absmax_kernel<<<grid, 256, 0, s>>>(x, N, pv, pi);
   CVS_CHECK_LAUNCH();
-  phase_apply_kernel<<<grid, 256, 0, s>>>(x, N, pv, pi, nb);
+  phase_pick_kernel<<<k, 32, 0, s>>>(x, N, pv, pi, nb, ph);
+  CVS_CHECK_LAUNCH();
+  phase_apply_kernel<<<grid, 256, 0, s>>>(x, N, ph);
   CVS_CHECK_LAUNCH();
 }
 

@@ -433,7 +433,8 @@ Dims dims_of(int M, int N, int K, int nprod) {
 
 bool tc_available() {
   static int avail = -1;
-  if (avail < 0) {
+  static std::once_flag once;
+  std::call_once(once, [] {
     int dev = 0, major = 0, minor = 0;
     avail = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -447,7 +448,7 @@ bool tc_available() {
       cudaFuncSetAttribute(tc_gemm_kernel,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            SMEM_BYTES);
-  }
+  });
   return avail == 1;
 }
 
@@ -554,8 +555,19 @@ constexpr int RUN_KT = 16;         // k-tiles per exact run: 16 * 64 = 1024 term
 constexpr int SLICE_BITS = 7;
 constexpr int MAX_PAIRS = 36;
 
-__constant__ int c_si[MAX_PAIRS];  // slice of A for pair p
-__constant__ int c_sj[MAX_PAIRS];  // slice of B for pair p
+// Slice pairs (i, j) ordered by order o = i + j, then by i.  With this
+// order the pairs of a 4-slice product (orders 0..3, 10 pairs) are the first
+// 10 of the 7-slice table (orders 0..6, 28 pairs), so one table, fixed at
+// compile time, serves both and no launch ever rewrites constant memory
+// under a kernel running on another stream.
+// slice of A for pair p
+__constant__ int c_si[MAX_PAIRS] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3,
+                                    0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5,
+                                    0, 1, 2, 3, 4, 5, 6};
+// slice of B for pair p
+__constant__ int c_sj[MAX_PAIRS] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0,
+                                    4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0,
+                                    6, 5, 4, 3, 2, 1, 0};
 
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
   // TwoSum without contraction
@@ -874,21 +886,6 @@ SDims sdims_of(int M, int N, int K, int nslices) {
   return d;
 }
 
-void upload_pairs(int nslices) {
-  static int loaded = -1;
-  if (loaded == nslices) return;
-  int si[MAX_PAIRS], sj[MAX_PAIRS], p = 0;
-  // by order o = i + j, then by i
-  for (int o = 0; o < nslices; ++o)
-    for (int i = 0; i <= o; ++i) {
-      si[p] = i;
-      sj[p] = o - i;
-      ++p;
-    }
-  CVS_CUDA(cudaMemcpyToSymbol(c_si, si, sizeof(int) * p));
-  CVS_CUDA(cudaMemcpyToSymbol(c_sj, sj, sizeof(int) * p));
-  loaded = nslices;
-}
 
 }  // namespace
 
@@ -905,14 +902,11 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
   SDims d = sdims_of(M, N, K, nslices);
   CVS_REQUIRE(work_bytes >= d.a_bytes + d.b_bytes + d.e_bytes, -1,
               "zgemm_slice: workspace too small");
-  static bool attr = false;
-  if (!attr) {
-    CVS_CUDA(cudaFuncSetAttribute(tc_slice_kernel,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  S_SMEM));
-    attr = true;
-  }
-  upload_pairs(nslices);
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(tc_slice_kernel,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, S_SMEM);
+  });
   __nv_bfloat16* ap = (__nv_bfloat16*)work;
   __nv_bfloat16* bp = (__nv_bfloat16*)((char*)work + d.a_bytes);
   int* eA = (int*)((char*)work + d.a_bytes + d.b_bytes);
