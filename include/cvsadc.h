@@ -183,6 +183,44 @@ int cvsadc_grad(cvsadc_ctx* ctx, const cvsadc_params* params,
                 double* omega, double* grad_eps, void* grad_B);
 
 /* --------------------------------------------------------------------
+ * cvsadc_solve_batched -- many independent problems of uneven size.
+ * Each instance i is what cvsadc_solve(params[i], eps[i], B[i], dip[i],
+ * omega[i], X[i], osc[i], &info[i]) computes (the paper solves one
+ * molecule at a time; batching is this library's addition).  The
+ * instances run on `lanes` worker contexts (0: 4), each with its own
+ * non-blocking stream and host thread, created on ctx's device at the
+ * first call and kept by ctx.  Instances are taken largest first and one is
+ * started when its estimated footprint (cvsadc_estimate_bytes) fits next to
+ * the running ones within 90 % of the device memory free at the call, or
+ * when nothing else runs; one that runs out of memory beside others is
+ * retried alone.  Which lane runs an instance, and when, does not change
+ * its result.
+ *   dip, X, osc, info, status : may be NULL (as a whole); entries of dip, X
+ *                               and osc may be NULL as in cvsadc_solve
+ *   status : [ninst] out, each instance's cvsadc_solve status
+ * Device inputs must be ready before the call (the lanes' streams wait on
+ * nothing).  Returns OK, ENOTCONV if any instance did not converge, or the
+ * first instance's negative error (cvsadc_last_error names it); every
+ * instance is attempted either way. */
+int cvsadc_solve_batched(cvsadc_ctx* ctx, int32_t ninst,
+                         const cvsadc_params* params, const double* const* eps,
+                         const void* const* B, const void* const* dip,
+                         double* const* omega, void* const* X,
+                         double* const* osc, cvsadc_info* info, int32_t* status,
+                         int32_t lanes);
+
+/* Upper estimate of the device bytes one cvsadc_solve of `params` holds at
+ * its peak (inputs, t2 and <ab||ij>, M11, the Davidson subspace, the sigma
+ * intermediates of the largest block, the tensor-core workspace), computed
+ * on the host without a GPU.  Errors: EINVAL for invalid params. */
+int cvsadc_estimate_bytes(const cvsadc_params* params, int64_t* bytes);
+
+/* Device bytes the buffers of ctx hold now (they persist between calls and
+ * are reused; the worker contexts of cvsadc_solve_batched are not counted).
+ * Errors: EINVAL for NULL arguments. */
+int cvsadc_device_bytes(cvsadc_ctx* ctx, int64_t* bytes);
+
+/* --------------------------------------------------------------------
  * Stage entry points.  cvsadc_prepare runs everything before the
  * eigen-solver and keeps the result in ctx; the calls below it then use
  * that prepared problem (CVSADC_ESTATE if there is none).

@@ -287,6 +287,82 @@ class Context:
         return dict(omega=omega, osc=osc if dip is not None else None, X=X,
                     info=info.as_dict(), status=rc)
 
+    def device_bytes(self):
+        """Bytes the context's device buffers hold (cvsadc_device_bytes)."""
+        out = ctypes.c_int64()
+        self._check(self.lib.cvsadc_device_bytes(self.h, ctypes.byref(out)))
+        return out.value
+
+    def solve_batched(self, instances, nroots, precision="fp64", tau=0.0, conv=1e-6,
+                      max_iter=0, return_x=False, refine=True, lanes=0):
+        """Independent problems through cvsadc_solve_batched.  `instances` is
+        a list of dicts with eps, B, dip (may be None), ncore, nval, nvirt
+        (numpy host arrays or torch CUDA tensors).  Returns one dict per
+        instance (omega, osc, X, info, status)."""
+        n = len(instances)
+        params = (Params * n)()
+        infos = (Info * n)()
+        keep, outs = [], []
+        ptrs = {k: (ctypes.c_void_p * n)() for k in ("eps", "B", "dip", "omega", "X", "osc")}
+        any_dip = False
+        for i, inst in enumerate(instances):
+            eps, B, dip = inst["eps"], inst["B"], inst.get("dip")
+            _inputs_ready(eps, B, dip)
+            pe, dev = _ptr(eps)
+            pb, _ = _ptr(B)
+            pd, _ = _ptr(dip)
+            nc, nw, nv = inst["ncore"], inst["nval"], inst["nvirt"]
+            flags = (CVSADC_FLAG_DEVICE_PTRS if dev else 0) | \
+                (CVSADC_FLAG_RETURN_X if return_x else 0) | \
+                (0 if refine else CVSADC_FLAG_NO_REFINE)
+            params[i] = self.params(nc, nw, nv, B.shape[0], nroots, precision, tau, conv,
+                                    max_iter, 0, flags)
+            if dev:
+                import torch
+                omega = torch.empty(nroots, dtype=torch.float64, device=eps.device)
+                osc = torch.empty(nroots, dtype=torch.float64, device=eps.device)
+            else:
+                omega, osc = np.empty(nroots), np.empty(nroots)
+            X = None
+            if return_x:
+                N = nc * nv + nc * nw * nv * (nv - 1) // 2
+                X = np.zeros(nroots * N, dtype=np.complex128)
+            ptrs["eps"][i], ptrs["B"][i] = pe, pb
+            ptrs["dip"][i] = pd
+            any_dip = any_dip or dip is not None
+            ptrs["omega"][i] = _ptr(omega)[0]
+            ptrs["osc"][i] = _ptr(osc)[0] if dip is not None else None
+            ptrs["X"][i] = ctypes.c_void_p(X.ctypes.data) if X is not None else None
+            keep.append((eps, B, dip))
+            outs.append((omega, osc if dip is not None else None, X, N if return_x else 0))
+        status = np.zeros(n, dtype=np.int32)
+        rc = self.lib.cvsadc_solve_batched(
+            self.h, n, params, ptrs["eps"], ptrs["B"], ptrs["dip"] if any_dip else None,
+            ptrs["omega"], ptrs["X"] if return_x else None, ptrs["osc"] if any_dip else None,
+            infos, ctypes.c_void_p(status.ctypes.data), lanes)
+        self._check(rc, allow_notconv=True)
+        res = []
+        for i, (omega, osc, X, N) in enumerate(outs):
+            if X is not None:
+                X = X.reshape(nroots, N)
+            res.append(dict(omega=omega, osc=osc, X=X, info=infos[i].as_dict(),
+                            status=int(status[i])))
+        return res
+
+
+def estimate_bytes(ncore, nval, nvirt, naux, nroots=4, precision="fp64", tau=0.0,
+                   max_subspace=0):
+    """cvsadc_estimate_bytes: device bytes one solve holds at its peak (host
+    arithmetic, no GPU needed)."""
+    lib = _lib.load()
+    p = Context.params(ncore, nval, nvirt, naux, nroots, precision, tau,
+                       max_subspace=max_subspace)
+    out = ctypes.c_int64()
+    rc = lib.cvsadc_estimate_bytes(ctypes.byref(p), ctypes.byref(out))
+    if rc != 0:
+        raise CvsadcError(rc, lib.cvsadc_strerror(rc).decode())
+    return out.value
+
 
 def energy_function(ctx, ncore, nval, nvirt, nroots, precision="fp64", conv=1e-8):
     """A torch.autograd.Function: E(eps, B) = sum of the lowest nroots

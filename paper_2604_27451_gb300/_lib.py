@@ -67,6 +67,12 @@ _SIGNATURES = {
                                     _vp, _vp, _vp, ctypes.POINTER(Info)]),
     "cvsadc_grad": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp, _vp, _vp,
                                    _vp]),
+    "cvsadc_solve_batched": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.POINTER(Params),
+                                            _vp, _vp, _vp, _vp, _vp, _vp,
+                                            ctypes.POINTER(Info), _vp, ctypes.c_int32]),
+    "cvsadc_estimate_bytes": (ctypes.c_int, [ctypes.POINTER(Params),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    "cvsadc_device_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
     "cvsadc_prepare": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp,
                                       ctypes.POINTER(Info)]),
     "cvsadc_prepared_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32),

@@ -33,7 +33,10 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <condition_variable>
 #include <new>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/cvsadc.h"
@@ -158,7 +161,26 @@ struct cvsadc_ctx {
   DBuf err;  // device int: non-zero after a bounded device wait expired
   DBuf s_kpart;  // split-K partial products
 
+  // worker contexts of cvsadc_solve_batched (own streams), kept for reuse
+  std::vector<cvsadc_ctx*> lanes;
+
   void sync() { CVS_CUDA(cudaStreamSynchronize(stream)); }
+  std::vector<DBuf*> problem_buffers() {
+    return {&eps,   &B,     &dip,   &t2,   &g2,     &M11,  &diag, &F,
+            &fns_occ, &fns_U, &s_big1, &s_big2, &s_S, &s_R, &s_Y, &s_V,
+            &s_part, &s_small, &s_tc, &dv_V, &dv_W, &dv_X, &dv_AX, &dv_T,
+            &dv_H,  &dv_A,  &dv_U,  &dv_w, &dv_misc};
+  }
+  // give back every problem-sized buffer (the context stays usable)
+  void trim() {
+    prepared = false;
+    for (DBuf* b : problem_buffers()) b->release();
+  }
+  size_t held_bytes() {
+    size_t t = s_kpart.bytes + err.bytes;
+    for (DBuf* b : problem_buffers()) t += b->bytes;
+    return t;
+  }
 };
 
 namespace {
@@ -1264,6 +1286,174 @@ int guarded(cvsadc_ctx* c, F&& f) {
 }  // namespace
 
 // =================================================================== C ABI
+// ------------------------------------------------------ batched solves
+namespace {
+
+// Device bytes one solve of `p` holds at its peak: inputs, t2 and <ab||ij>,
+// the (ai|bj) band, M11 and its build scratch, the Davidson subspace and
+// block vectors, the sigma intermediates of its largest block (the initial
+// guesses), the tensor-core packing workspace of the largest contraction
+// and the split-K scratch.  Host arithmetic only; used to admit instances
+// of a batch to the GPU and offered to callers that size their own memory.
+double estimate_bytes(const cvsadc_params* p) {
+  const double z = sizeof(cplx);
+  const double nc = p->ncore, nw = p->nval, v = p->nvirt, L = p->naux;
+  const double o = nc + nw, n = o + v;
+  const double N1 = nc * v, wv = nw * v, N = N1 + nc * nw * v * (v - 1) / 2;
+  const int k = std::max(1, p->nroots);
+  const int msub = std::min(p->max_subspace > 0 ? p->max_subspace
+                                                : std::max(8 * k, 48), 128);
+  const int ms = std::max(msub, 2 * k + 2);
+  const int nkeep = std::max(k, std::min(ms / 3, ms - 2 * k));
+  const double g = std::min(64, std::max(k, std::min(2 * k, ms / 2)));
+  double b = 8 * n + z * L * n * n;
+  b += 3 * z * n * n;                       // dipoles
+  b += 2 * z * o * o * v * v;               // t2, <ab||ij>
+  if (p->fns_threshold > 0) b += 2 * z * o * o * v * v + 2 * z * v * v;
+  const double band = std::min(4.0 * (1 << 30), z * o * v * o * v);
+  b += std::max(band, z * g * N1 * wv);     // s_big1
+  b += std::max({z * (v * v * nc * nc + 2 * N1 * N1 + v * v + nc * nc),
+                 z * g * N1 * wv, 2 * z * nc * nw * v * v});  // s_big2
+  b += z * N1 * N1 + 8 * N;                 // M11, diagonal
+  b += 2 * z * g * N1 * L + 2 * z * g * wv * L;  // S, Y, R, V
+  b += z * N * (2.0 * ms + 2.0 * nkeep + k);  // Davidson V, W, X, AX, T
+  b += z * (double)ms * ms * 320 + 1e6;     // subspace matrices, partials
+  b += 3 * z * N;                           // moments
+  if (p->precision != CVSADC_FP64) {
+    const int ns = p->precision == CVSADC_MIXED_SLICE4 ? 4
+                   : p->precision == CVSADC_FP64_SLICE7 ? 7 : 0;
+    auto ws = [&](double M, double Nn, double K, int nsl) {
+      if (M < 32 || K < 64 || M * Nn * K < 1e7) return 0.0;
+      return (double)(nsl ? slice_workspace_bytes((int)M, (int)Nn, (int)K, nsl)
+                          : tc_workspace_bytes((int)M, (int)Nn, (int)K, 3));
+    };
+    const double na = std::max(1.0, std::min(v, std::floor(band / (z * o * v * o))));
+    double w = 0;
+    for (double s : {ws(na * o, v * o, L, ns), ws(N1, N1, L, ns), ws(N1, N1, o * v, ns),
+                     ws(g * N1, L, wv, ns), ws(g * wv, L, N1, ns), ws(g * N1, wv, L, ns),
+                     ws(N1, g * wv, L, ns)})
+      w = std::max(w, s);
+    // a mixed precision is refined with the 7-slice product
+    if (needs_refine(p->precision))
+      for (double s : {ws(k * N1, L, wv, 7), ws(k * wv, L, N1, 7), ws(k * N1, wv, L, 7),
+                       ws(N1, k * wv, L, 7)})
+        w = std::max(w, s);
+    b += w;
+  }
+  b += (double)(8 << 20) * z + 1024;        // split-K scratch, error flag
+  return 1.1 * b + (64 << 20);
+}
+
+struct BatchJob {
+  int idx;
+  double bytes;
+  bool solo;  // admitted only onto an otherwise idle GPU
+};
+
+// Runs the instances on `lanes` worker contexts (each its own stream and
+// host thread).  Jobs are taken largest first; a job is admitted when its
+// estimated footprint fits next to the running ones within `budget`, or
+// when nothing else runs.  A job that still runs out of memory beside
+// others is put back to run alone.
+void solve_batched_impl(cvsadc_ctx* c, int ninst, const cvsadc_params* params,
+                        const double* const* eps, const void* const* B,
+                        const void* const* dip, double* const* omega,
+                        void* const* X, double* const* osc, cvsadc_info* info,
+                        int32_t* status, int lanes) {
+  std::vector<BatchJob> queue;
+  for (int i = 0; i < ninst; ++i) {
+    validate(&params[i]);
+    CVS_REQUIRE(eps[i] && B[i] && omega[i], CVSADC_EINVAL,
+                "batched: eps, B and omega are required for every instance");
+    queue.push_back({i, estimate_bytes(&params[i]), false});
+  }
+  std::stable_sort(queue.begin(), queue.end(),
+                   [](const BatchJob& a, const BatchJob& b) { return a.bytes > b.bytes; });
+  size_t free_b = 0, total_b = 0;
+  CVS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const double budget = 0.9 * (double)free_b;
+  lanes = std::max(1, std::min(lanes, ninst));
+  while ((int)c->lanes.size() < lanes) {
+    cvsadc_ctx* l = nullptr;
+    int rc = cvsadc_create(&l, c->device, nullptr);
+    CVS_REQUIRE(rc == CVSADC_OK, rc, "batched: could not create a worker context");
+    c->lanes.push_back(l);
+  }
+  std::vector<int> rcs(ninst, CVSADC_OK);
+  std::vector<std::string> msgs(ninst);
+  std::mutex mu;
+  std::condition_variable cv;
+  double in_use = 0;
+  int running = 0;
+  auto worker = [&](cvsadc_ctx* lane) {
+    cudaSetDevice(c->device);
+    for (;;) {
+      BatchJob job{-1, 0, false};
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+          if (queue.empty()) return;
+          auto it = queue.end();
+          if (running == 0) {
+            it = queue.begin();
+          } else {
+            for (auto q = queue.begin(); q != queue.end(); ++q)
+              if (!q->solo && in_use + q->bytes <= budget) {
+                it = q;
+                break;
+              }
+          }
+          if (it != queue.end()) {
+            job = *it;
+            queue.erase(it);
+            break;
+          }
+          cv.wait(lk);
+        }
+        in_use += job.bytes;
+        ++running;
+      }
+      const int i = job.idx;
+      int rc = cvsadc_solve(lane, &params[i], eps[i], B[i], dip ? dip[i] : nullptr,
+                            omega[i], X ? X[i] : nullptr, osc ? osc[i] : nullptr,
+                            info ? &info[i] : nullptr);
+      std::string msg = rc == CVSADC_OK ? "" : lane->last_error;
+      lane->trim();
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        in_use -= job.bytes;
+        --running;
+        if (rc == CVSADC_ENOMEM && !job.solo) {
+          job.solo = true;
+          queue.insert(queue.begin(), job);
+        } else {
+          rcs[i] = rc;
+          msgs[i] = msg;
+        }
+      }
+      cv.notify_all();
+    }
+  };
+  std::vector<std::thread> th;
+  for (int l = 0; l < lanes; ++l) th.emplace_back(worker, c->lanes[l]);
+  for (auto& t : th) t.join();
+  int worst = CVSADC_OK;
+  for (int i = 0; i < ninst; ++i) {
+    if (status) status[i] = rcs[i];
+    if (rcs[i] < 0 && worst >= 0) {
+      worst = rcs[i];
+      c->last_error = "instance " + std::to_string(i) + ": " + msgs[i];
+    } else if (rcs[i] == CVSADC_ENOTCONV && worst == CVSADC_OK) {
+      worst = CVSADC_ENOTCONV;
+    }
+  }
+  if (worst < 0) throw Error{worst, c->last_error};
+  if (worst == CVSADC_ENOTCONV)
+    throw Error{CVSADC_ENOTCONV, "some instances did not converge"};
+}
+
+}  // namespace
+
 extern "C" {
 
 int cvsadc_create(cvsadc_ctx** ctx, int device, void* cuda_stream) {
@@ -1301,6 +1491,8 @@ int cvsadc_create(cvsadc_ctx** ctx, int device, void* cuda_stream) {
 
 void cvsadc_destroy(cvsadc_ctx* c) {
   if (!c) return;
+  for (cvsadc_ctx* l : c->lanes) cvsadc_destroy(l);
+  c->lanes.clear();
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1495,6 +1687,39 @@ int cvsadc_solve(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   rc = guarded(c, [&] { davidson_entry(c, p, omega, X, osc, info); });
   if (info) info->t_total_ms = now_ms() - t0;
   return rc;
+}
+
+int cvsadc_estimate_bytes(const cvsadc_params* p, int64_t* bytes) {
+  if (!p || !bytes) return CVSADC_EINVAL;
+  try {
+    validate(p);
+    *bytes = (int64_t)estimate_bytes(p);
+    return CVSADC_OK;
+  } catch (const Error& e) {
+    return e.code;
+  } catch (...) {
+    return CVSADC_EINVAL;
+  }
+}
+
+int cvsadc_device_bytes(cvsadc_ctx* c, int64_t* bytes) {
+  if (!c || !bytes) return CVSADC_EINVAL;
+  *bytes = (int64_t)c->held_bytes();
+  return CVSADC_OK;
+}
+
+int cvsadc_solve_batched(cvsadc_ctx* c, int32_t ninst, const cvsadc_params* params,
+                         const double* const* eps, const void* const* B,
+                         const void* const* dip, double* const* omega,
+                         void* const* X, double* const* osc, cvsadc_info* info,
+                         int32_t* status, int32_t lanes) {
+  if (!c || ninst < 0 || (ninst > 0 && (!params || !eps || !B || !omega)))
+    return CVSADC_EINVAL;
+  if (ninst == 0) return CVSADC_OK;
+  return guarded(c, [&] {
+    solve_batched_impl(c, ninst, params, eps, B, dip, omega, X, osc, info, status,
+                       lanes > 0 ? lanes : 4);
+  });
 }
 
 }  // extern "C"

@@ -59,3 +59,37 @@ def test_create_without_gpu_fails_cleanly(lib):
     rc = lib.cvsadc_create(ctypes.byref(h), 0, None)
     assert rc in (-1, -4)
     assert not h.value
+
+
+def test_estimate_bytes_without_gpu():
+    """The footprint estimate is host arithmetic: it bounds the stored
+    tensors from below and grows with every dimension and the root count."""
+    import paper_2604_27451_gb300 as pkg
+
+    def est(nc, nw, nv, L, k=4, prec="fp64"):
+        return pkg.estimate_bytes(nc, nw, nv, L, nroots=k, precision=prec)
+
+    nc, nw, nv, L = 6, 50, 250, 1250
+    n, o = nc + nw + nv, nc + nw
+    N = nc * nv + nc * nw * nv * (nv - 1) // 2
+    floor = 16 * L * n * n + 32 * o * o * nv * nv + 16 * N * 48 * 2
+    assert est(nc, nw, nv, L) >= floor
+    assert est(nc, nw, nv, L) < 3 * floor
+    assert est(nc, nw, nv + 10, L) > est(nc, nw, nv, L)
+    assert est(nc, nw + 2, nv, L) > est(nc, nw, nv, L)
+    assert est(nc, nw, nv, L + 100) > est(nc, nw, nv, L)
+    assert est(nc, nw, nv, L, k=16) > est(nc, nw, nv, L, k=4)
+    # the tensor-core precisions add a packing workspace
+    assert est(nc, nw, nv, L, prec="slice4") > est(nc, nw, nv, L)
+    with pytest.raises(pkg.CvsadcError):
+        est(0, nw, nv, L)
+
+
+def test_batched_and_bytes_reject_null_without_gpu():
+    from paper_2604_27451_gb300 import _lib
+
+    lib = _lib.load()
+    assert lib.cvsadc_solve_batched(None, 1, None, None, None, None, None, None, None,
+                                    None, None, 0) == -1
+    assert lib.cvsadc_device_bytes(None, None) == -1
+    assert lib.cvsadc_estimate_bytes(None, None) == -1
