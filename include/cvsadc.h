@@ -88,6 +88,9 @@ extern "C" {
 #define CVSADC_FLAG_RETURN_X 2     /* write eigenvectors to X */
 #define CVSADC_FLAG_NO_REFINE 4    /* mixed path: skip the FP64 residual
                                       correction sweep */
+#define CVSADC_FLAG_DIAG_PRECOND 8 /* Davidson with the diagonal
+                                      preconditioner only (no Schur
+                                      complement) */
 
 typedef struct {
   int32_t ncore, nval, nvirt, naux;
@@ -120,6 +123,12 @@ typedef struct {
   double t_refine_ms;      /* FP64 residual correction */
   double t_total_ms;
   double t_sigma_ms;       /* device time of the sigma builds (CUDA events) */
+  double t_schur_ms;       /* building the Schur-complement preconditioner */
+  double schur_theta;      /* its trial energy theta0 (0: not used) */
+  int32_t coupling_vectors;/* one-sided coupling products M21 x1 or M12 x2
+                              done by the preconditioner (two make one
+                              sigma's worth of work) */
+  int32_t schur_builds;    /* S(theta) evaluations of the theta0 search */
 } cvsadc_info;
 
 typedef struct cvsadc_ctx cvsadc_ctx;
@@ -251,6 +260,15 @@ int cvsadc_get_m11(cvsadc_ctx* ctx, int32_t flags, void* m11);
  * and U [nvirt_in][nvirt_kept] complex; either may be NULL.  Only valid
  * when the problem was prepared with tau > 0. */
 int cvsadc_get_fns(cvsadc_ctx* ctx, int32_t flags, double* occ, void* U);
+
+/* The singles block with the doubles folded in at a trial energy theta,
+ * S(theta) = M11 + M12 (theta - M22)^-1 M21, [N1][N1] complex (row-major),
+ * computed in FP64 from the prepared problem.  Exact because M22 is
+ * diagonal: an eigenvalue w of M below every M22 entry is an eigenvalue of
+ * S(w).  The Davidson solver uses S(theta0) as its preconditioner (see
+ * cvsadc_info.schur_theta); this call exposes it for inspection and tests.
+ * theta must differ from every M22 entry.  Memory space per `flags`. */
+int cvsadc_get_schur(cvsadc_ctx* ctx, double theta, int32_t flags, void* S);
 
 /* Modified transition moments F [3][N] complex, through first order. */
 int cvsadc_get_moments(cvsadc_ctx* ctx, int32_t flags, void* F);

@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    CVSADC_FLAG_DEVICE_PTRS, CVSADC_FLAG_NO_REFINE, CVSADC_FLAG_RETURN_X,
+    CVSADC_FLAG_DEVICE_PTRS, CVSADC_FLAG_DIAG_PRECOND, CVSADC_FLAG_NO_REFINE,
+    CVSADC_FLAG_RETURN_X,
     CVSADC_FP64, CVSADC_MIXED_BF16X3, CVSADC_ENOTCONV, Info, Params,
 )
 
@@ -146,6 +147,14 @@ class Context:
         self._check(self.lib.cvsadc_get_m11(self.h, 0, ctypes.c_void_p(m.ctypes.data)))
         return m
 
+    def get_schur(self, theta):
+        """S(theta) = M11 + M12 (theta - M22)^-1 M21 of the prepared problem."""
+        n1 = self._shape["N1"]
+        S = np.empty((n1, n1), dtype=np.complex128)
+        self._check(self.lib.cvsadc_get_schur(self.h, ctypes.c_double(theta), 0,
+                                              ctypes.c_void_p(S.ctypes.data)))
+        return S
+
     def get_moments(self):
         F = np.empty((3, self._shape["N"]), dtype=np.complex128)
         self._check(self.lib.cvsadc_get_moments(self.h, 0, ctypes.c_void_p(F.ctypes.data)))
@@ -197,9 +206,10 @@ class Context:
         return C
 
     def davidson(self, nroots, precision="fp64", conv=1e-6, max_iter=0,
-                 max_subspace=0, return_x=False, refine=True):
+                 max_subspace=0, return_x=False, refine=True, precond="schur"):
         s = self._shape
-        flags = (CVSADC_FLAG_RETURN_X if return_x else 0) | \
+        flags = (CVSADC_FLAG_DIAG_PRECOND if precond == "diag" else 0) | \
+            (CVSADC_FLAG_RETURN_X if return_x else 0) | \
             (0 if refine else CVSADC_FLAG_NO_REFINE)
         p = self.params(s["ncore"], s["nval"], s["nvirt"], s["naux"], nroots,
                         precision, 0.0, conv, max_iter, max_subspace, flags)
@@ -243,7 +253,7 @@ class Context:
 
     def solve(self, eps, B, dip, ncore, nval, nvirt, nroots, precision="fp64",
               tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, return_x=False,
-              refine=True, refine_sweeps=0):
+              refine=True, refine_sweeps=0, precond="schur"):
         """The whole path through cvsadc_solve."""
         naux = B.shape[0]
         _inputs_ready(eps, B, dip)
@@ -252,7 +262,8 @@ class Context:
         pd, _ = _ptr(dip)
         flags = (CVSADC_FLAG_DEVICE_PTRS if dev else 0) | \
             (CVSADC_FLAG_RETURN_X if return_x else 0) | \
-            (0 if refine else CVSADC_FLAG_NO_REFINE)
+            (0 if refine else CVSADC_FLAG_NO_REFINE) | \
+            (CVSADC_FLAG_DIAG_PRECOND if precond == "diag" else 0)
         p = self.params(ncore, nval, nvirt, naux, nroots, precision, tau, conv,
                         max_iter, max_subspace, flags, refine_sweeps)
         if dev:

@@ -30,6 +30,7 @@ CVSADC_FP64_SLICE7 = 3
 CVSADC_FLAG_DEVICE_PTRS = 1
 CVSADC_FLAG_RETURN_X = 2
 CVSADC_FLAG_NO_REFINE = 4
+CVSADC_FLAG_DIAG_PRECOND = 8
 
 
 class Params(ctypes.Structure):
@@ -50,7 +51,9 @@ class Info(ctypes.Structure):
         ("emp2", ctypes.c_double), ("max_residual", ctypes.c_double),
         ("t_prepare_ms", ctypes.c_double), ("t_davidson_ms", ctypes.c_double),
         ("t_refine_ms", ctypes.c_double), ("t_total_ms", ctypes.c_double),
-        ("t_sigma_ms", ctypes.c_double),
+        ("t_sigma_ms", ctypes.c_double), ("t_schur_ms", ctypes.c_double),
+        ("schur_theta", ctypes.c_double), ("coupling_vectors", ctypes.c_int32),
+        ("schur_builds", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -73,6 +76,7 @@ _SIGNATURES = {
     "cvsadc_estimate_bytes": (ctypes.c_int, [ctypes.POINTER(Params),
                                              ctypes.POINTER(ctypes.c_int64)]),
     "cvsadc_device_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "cvsadc_get_schur": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int32, _vp]),
     "cvsadc_prepare": (ctypes.c_int, [_vp, ctypes.POINTER(Params), _vp, _vp, _vp,
                                       ctypes.POINTER(Info)]),
     "cvsadc_prepared_sizes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int32),

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libcvsadc.so")
 SOURCES = ["gemm_f64.cu", "gemm_tc.cu", "elementwise.cu", "jacobi.cu", "solver.cu",
-           "noalloc.cu", "grad_kernels.cu"]
+           "noalloc.cu", "grad_kernels.cu", "schur_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "--expt-relaxed-constexpr", "-I", CSRC, "-I", INCLUDE]

@@ -196,11 +196,13 @@ __global__ void sigma2_kernel(const cplx* __restrict__ G,
       cplx g1 = Ga[b];
       cplx g2 = G[(((int64_t)I * nv + b) * nw + j) * nv + a];
       int64_t d = base + b;
-      cplx x = x2[d];
-      double m22 = e0 + eps[o + b];
       cplx out = csub(g2, g1);
-      out.x += m22 * x.x;
-      out.y += m22 * x.y;
+      if (x2) {  // without x2: the coupling M21 x1 alone
+        cplx x = x2[d];
+        double m22 = e0 + eps[o + b];
+        out.x += m22 * x.x;
+        out.y += m22 * x.y;
+      }
       s2[d] = out;
     }
   }
@@ -411,6 +413,10 @@ __global__ void resid_kernel(const cplx* __restrict__ AX,
     cplx x = X[(int64_t)r * N + n];
     cplx res = cmake(ax.x - th * x.x, ax.y - th * x.y);
     acc += res.x * res.x + res.y * res.y;
+    if (!diag) {  // the raw residual, for a preconditioner applied later
+      t[(int64_t)r * N + n] = res;
+      continue;
+    }
     double den = th - diag[n];
     if (fabs(den) < 1e-4) den = den < 0 ? -1e-4 : 1e-4;
     t[(int64_t)r * N + n] = cscale(res, 1.0 / den);

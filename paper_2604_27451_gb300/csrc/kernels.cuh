@@ -150,4 +150,31 @@ void herm_project(cudaStream_t s, cplx* G, int n, int64_t nmat);
 void jacobi_eigh(cudaStream_t s, cplx* A, int n, double* w, cplx* Vec,
                  int max_sweeps, double* info_dev);
 
+// Schur-complement preconditioner (schur_kernels.cu)
+void h_assemble(cudaStream_t s, const cplx* hc1, const cplx* hc2, int nc,
+                int nw, int nv, cplx* h);
+void g_assemble(cudaStream_t s, const cplx* X1, const cplx* X2, int jc, int nv,
+                cplx* G);
+void g_weight(cudaStream_t s, const cplx* G, int jc, int j0, int nc, int nw,
+              int nv, const double* eps, double theta, cplx* Gw);
+void h_weight(cudaStream_t s, const cplx* h, int j, int nc, int nw, int nv,
+              const double* eps, double theta, cplx* Hw);
+void schur_assemble(cudaStream_t s, const cplx* M11, const cplx* C11,
+                    const cplx* C12, const cplx* h, int nc, int nw, int nv,
+                    const double* eps, double theta, cplx* S22, cplx* S);
+int jacobi_eigh_parallel(cudaStream_t s, cplx* A, int n, double* w, cplx* U,
+                         cplx* V, double* part, double* cc, cplx* se,
+                         int max_sweeps);
+void fold_doubles(cudaStream_t s, const cplx* R, const cplx* U2,
+                  const double* theta, int k, int64_t N, int64_t N1, int nc,
+                  int nw, int nv, const double* eps, bool zero_singles,
+                  cplx* out);
+double fold_norm(cudaStream_t s, const cplx* u, int64_t N, int64_t N1, int nc,
+                 int nw, int nv, const double* eps, double theta,
+                 double* part);
+void eig_shift(cudaStream_t s, cplx* Y, int64_t n1, int k, const double* lam,
+               const double* theta);
+void add_singles(cudaStream_t s, const cplx* a, const cplx* b, int64_t N,
+                 int64_t n1, int k, cplx* out);
+
 }  // namespace cvs

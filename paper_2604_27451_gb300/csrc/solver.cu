@@ -161,6 +161,13 @@ struct cvsadc_ctx {
   DBuf err;  // device int: non-zero after a bounded device wait expired
   DBuf s_kpart;  // split-K partial products
 
+  // Schur-complement preconditioner of the prepared problem
+  DBuf sch_h, sch_g, sch_S, sch_U, sch_V, sch_lam, sch_C11, sch_C12, sch_work,
+      sch_tmp, sch_th;
+  bool sch_on = false;
+  double sch_theta = 0.0, sch_ms = 0.0;
+  int sch_builds = 0, sch_couplings = 0;
+
   // worker contexts of cvsadc_solve_batched (own streams), kept for reuse
   std::vector<cvsadc_ctx*> lanes;
 
@@ -169,12 +176,15 @@ struct cvsadc_ctx {
     return {&eps,   &B,     &dip,   &t2,   &g2,     &M11,  &diag, &F,
             &fns_occ, &fns_U, &s_big1, &s_big2, &s_S, &s_R, &s_Y, &s_V,
             &s_part, &s_small, &s_tc, &dv_V, &dv_W, &dv_X, &dv_AX, &dv_T,
-            &dv_H,  &dv_A,  &dv_U,  &dv_w, &dv_misc};
+            &dv_H,  &dv_A,  &dv_U,  &dv_w, &dv_misc, &sch_h, &sch_g,
+            &sch_S, &sch_U, &sch_V, &sch_lam, &sch_C11, &sch_C12, &sch_work,
+            &sch_tmp, &sch_th};
   }
   // give back every problem-sized buffer (the context stays usable)
   void trim() {
     prepared = false;
     for (DBuf* b : problem_buffers()) b->release();
+    sch_on = false;
   }
   size_t held_bytes() {
     size_t t = s_kpart.bytes + err.bytes;
@@ -409,7 +419,12 @@ void build_moments(cvsadc_ctx* c, int prec) {
 // sigma for a group of g vectors at once: every contraction runs over the
 // whole group, so the ncore-sized dimensions become g * ncore and operands
 // built from B^P are packed once per group.
-void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g) {
+// mode SIG_FULL: sigma = M x.  SIG_FWD: only the doubles part, sigma2 =
+// M21 x1 (no M22 term, singles part untouched).  SIG_ADJ: only the singles
+// part, sigma1 = M12 x2 (no M11 term, doubles part untouched).
+enum { SIG_FULL = 0, SIG_FWD = 1, SIG_ADJ = 2 };
+void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
+                 int mode = SIG_FULL) {
   const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
             L = c->naux;
   const int64_t nn = (int64_t)n * n, N1 = c->N1, N = c->N;
@@ -428,6 +443,7 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g) {
   cplx* R = c->s_R.c();      // [(q,c,j)][P]
   cplx* Y = c->s_Y.c();      // [(q,I,a)][P]
   cplx* Vv = c->s_V.c();     // [(q,j,b)][P]
+  if (mode != SIG_FWD) {
   for (int q = 0; q < g; ++q)
     unpack_doubles(c->stream, x + q * N + N1, nc, nw, v, Yt + q * N1wv);
   // S[(q,I,a)][P] = sum_{jb} y_{Ijab} B^P_{jb}
@@ -450,6 +466,8 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g) {
        rows2(view(B, 0, 1), n, nn, L), 1.0, s1t);
   gemm(c, prec, g * v, nc, nw * L, -1.0, view(R, (int64_t)nw * L, 1),
        rows2(view(B + (int64_t)nc * n, 0, 1), n, nn, L), 1.0, s1t);
+  }
+  if (mode == SIG_ADJ) return;
   // Y[(q,I,a)][P] = sum_c x_Ic B^P_ac - sum_K x_Ka B^P_KI
   gemm(c, prec, g * nc, (int)vL, v, 1.0, rows2(view(x, 0, 1), N, v, nc),
        cols2(view(B + (int64_t)o * n + o, 1, 0), n, nn, L), 0.0,
@@ -469,21 +487,24 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g) {
        rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v), view(Vv, 1, L), 1.0,
        cols2(view(G, wv, 0), N1wv, 1, (int)wv));
   for (int q = 0; q < g; ++q)
-    sigma2_finish(c->stream, G + q * N1wv, x + q * N + N1, c->eps.d(), nc, nw,
-                  v, sig + q * N + N1);
+    sigma2_finish(c->stream, G + q * N1wv,
+                  mode == SIG_FWD ? nullptr : x + q * N + N1, c->eps.d(), nc,
+                  nw, v, sig + q * N + N1);
+  if (mode == SIG_FWD) return;
   // sigma1 += M11 x1 (dense product, FP64 for the small block)
   gemm64(c, (int)N1, g, (int)N1, 1.0, view(c->M11.c(), N1, 1), view(x, 1, N),
          1.0, view(sig, 1, N));
 }
 
-void sigma_impl(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int nvec) {
+void sigma_impl(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int nvec,
+                int mode = SIG_FULL) {
   const int64_t N1 = c->N1, wv = (int64_t)c->nval * c->nvirt, L = c->naux;
   const double per_vec = (2.0 * N1 * wv + 2.0 * N1 * L + 2.0 * wv * L) * sizeof(cplx);
   const double budget = 48e9;
   int g = (int)std::max(1.0, std::min((double)nvec, budget / per_vec));
   for (int q0 = 0; q0 < nvec; q0 += g) {
     const int gg = std::min(g, nvec - q0);
-    sigma_group(c, prec, x + q0 * c->N, sig + q0 * c->N, gg);
+    sigma_group(c, prec, x + q0 * c->N, sig + q0 * c->N, gg, mode);
   }
 }
 
@@ -636,6 +657,8 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   double t0 = now_ms();
   bool dev = (p->flags & CVSADC_FLAG_DEVICE_PTRS) != 0;
   c->prepared = false;
+  c->sch_on = false;
+  c->sch_g.release();
   c->ncore = p->ncore;
   c->nval = p->nval;
   c->nvirt_in = c->nvirt = p->nvirt;
@@ -682,6 +705,262 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   }
 }
 
+// ------------------------------------------- Schur-complement preconditioner
+// Because M22 is diagonal, the doubles fold into the singles exactly:
+// S(theta) = M11 + M12 (theta - M22)^-1 M21 (schur_kernels.cu gives the five
+// pieces of the second term).  The Davidson solver takes the eigen-
+// decomposition S(theta0) = U diag(lam) U^H at a trial energy theta0 near
+// the lowest root and uses it twice: its lowest eigenvectors, with their
+// folded doubles (theta0 - M22)^-1 M21 u, are the initial guesses, and a
+// residual (r1, r2) of a root with Ritz value theta is corrected by block
+// elimination with S(theta0) in place of S(theta):
+//   t1 = U (theta - lam)^-1 U^H [r1 + M12 (theta - M22)^-1 r2]
+//   t2 = (theta - M22)^-1 (r2 + M21 t1).
+// This is a preconditioner only: its arithmetic (the tensor-core precision
+// where available) leaves the converged roots unchanged.
+
+// the preconditioner's GEMM precision
+int schur_precision() {
+  return tc_available() ? CVSADC_MIXED_SLICE4 : CVSADC_FP64;
+}
+
+// <ab||cj> for j in [j0, j0 + jc) into G[jl][a][b][c]; X1, X2 hold
+// jc v^3 complex each
+void build_g_chunk(cvsadc_ctx* c, int prec, int j0, int jc, cplx* X1, cplx* X2,
+                   cplx* G) {
+  const int nc = c->ncore, v = c->nvirt, o = c->o, n = c->n, L = c->naux;
+  const int64_t nn = (int64_t)n * n;
+  const cplx* B = c->B.c();
+  // X1[(a,c)][(jl,b)] = sum_P B^P_ac B^P_bj
+  gemm(c, prec, v * v, jc * v, L, 1.0,
+       rows2(view(B + (int64_t)o * n + o, 0, nn), n, 1, v),
+       cols2(view(B + (int64_t)o * n + nc + j0, nn, 0), 1, n, v), 0.0,
+       view(X1, (int64_t)jc * v, 1));
+  // X2[(jl,a)][(b,c)] = sum_P B^P_aj B^P_bc
+  gemm(c, prec, jc * v, v * v, L, 1.0,
+       rows2(view(B + (int64_t)o * n + nc + j0, 0, nn), 1, n, v),
+       cols2(view(B + (int64_t)o * n + o, nn, 0), n, 1, v), 0.0,
+       view(X2, (int64_t)v * v, 1));
+  g_assemble(c->stream, X1, X2, jc, v, G);
+}
+
+// j per chunk so that the chunk buffers (X1, X2, G and ncore weighted
+// copies) stay within ~6 GB
+int schur_jchunk(cvsadc_ctx* c) {
+  const double per_j = (3.0 + c->ncore) * std::pow((double)c->nvirt, 3) * sizeof(cplx);
+  return (int)std::max(1.0, std::min((double)c->nval, 6e9 / per_j));
+}
+
+// S(theta) into sch_S, then its eigen-decomposition into sch_U / sch_lam
+void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached) {
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt;
+  const int64_t N1 = c->N1, v3 = (int64_t)v * v * v;
+  cudaStream_t s = c->stream;
+  const int jc = schur_jchunk(c);
+  CVS_CUDA(cudaMemsetAsync(c->sch_C11.p, 0, (size_t)nc * v * v * sizeof(cplx), s));
+  CVS_CUDA(cudaMemsetAsync(c->sch_C12.p, 0,
+                           (size_t)v * v * nc * nc * sizeof(cplx), s));
+  // chunk buffers: [X1 | X2 | G | Gw (ncore copies)] (X1, X2, G unused when
+  // cached)
+  cplx* X1 = c->sch_work.c();
+  cplx* X2 = X1 + (int64_t)jc * v3;
+  cplx* Gt = X2 + (int64_t)jc * v3;
+  cplx* Gw = Gt + (int64_t)jc * v3;
+  cplx* Hw = c->sch_tmp.c();
+  const bool vb = verbose();
+  double tv = vb ? (c->sync(), now_ms()) : 0.0, t11 = 0.0, t12 = 0.0;
+  for (int j0 = 0; j0 < nw; j0 += jc) {
+    const int jn = std::min(jc, nw - j0);
+    cplx* G = Gt;
+    if (cached)
+      G = c->sch_g.c() + (int64_t)j0 * v3;
+    else
+      build_g_chunk(c, prec, j0, jn, X1, X2, Gt);
+    // (11): C11[(K,c)][c'] += sum_{jab} 1/2 w_Kjab conj(g_abc) g_abc', all K
+    // in one GEMM (rows (K, c) of the weighted copies)
+    g_weight(s, G, jn, j0, nc, nw, v, c->eps.d(), theta, Gw);
+    gemm(c, prec, nc * v, v, jn * v * v, 1.0,
+         conj_of(rows2(view(Gw, 0, v), (int64_t)jn * v3, 1, v)), view(G, v, 1),
+         1.0, view(c->sch_C11.c(), v, 1));
+    if (vb) {
+      c->sync();
+      t11 += now_ms() - tv;
+      tv = now_ms();
+    }
+    // (12): C12[c'][c][K][K'] += sum_b conj(<c'b||cj>) w_{Kjc'b} <K'b||Kj>
+    for (int jl = 0; jl < jn; ++jl) {
+      h_weight(s, c->sch_h.c(), j0 + jl, nc, nw, v, c->eps.d(), theta, Hw);
+      gemm(c, CVSADC_FP64, v, nc * nc, v, 1.0,
+           batched(conj_of(view(G + (int64_t)jl * v3, 1, v)), (int64_t)v * v),
+           batched(view(Hw, nc * nc, 1), (int64_t)v * nc * nc), 1.0,
+           batched(view(c->sch_C12.c(), nc * nc, 1), (int64_t)v * nc * nc), v);
+    }
+    if (vb) {
+      c->sync();
+      t12 += now_ms() - tv;
+      tv = now_ms();
+    }
+  }
+  schur_assemble(s, c->M11.c(), c->sch_C11.c(), c->sch_C12.c(), c->sch_h.c(), nc,
+                 nw, v, c->eps.d(), theta, c->sch_V.c(), c->sch_S.c());
+  if (vb) {
+    c->sync();
+    fprintf(stderr, "[cvsadc] schur build: (11) %.1f ms  (12) %.1f ms  assemble %.1f ms\n",
+            t11, t12, now_ms() - tv);
+  }
+}
+
+// scratch of sch_th (doubles): [0,128) per-root theta, [128, 736) partial
+// sums, then the rotation cosines and (16-byte aligned) the sines
+size_t schur_th_doubles(int64_t N1) {
+  const size_t cc_n = (size_t)(N1 / 2 + 2);
+  return 736 + ((cc_n + 1) & ~(size_t)1) + 2 * cc_n;
+}
+
+void schur_eigh(cvsadc_ctx* c) {
+  const double t0 = verbose() ? (c->sync(), now_ms()) : 0.0;
+  const int64_t N1 = c->N1;
+  const size_t cc_n = (size_t)(N1 / 2 + 2);
+  double* part = c->sch_th.d() + 128;
+  double* cc = c->sch_th.d() + 736;
+  cplx* se = (cplx*)(c->sch_th.d() + 736 + ((cc_n + 1) & ~(size_t)1));
+  const int sweeps =
+      jacobi_eigh_parallel(c->stream, c->sch_S.c(), (int)N1, c->sch_lam.d(),
+                           c->sch_U.c(), c->sch_V.c(), part, cc, se, 30);
+  ++c->sch_builds;
+  if (verbose()) {
+    c->sync();
+    fprintf(stderr, "[cvsadc] schur eigh n %lld: %d sweeps, %.1f ms\n",
+            (long long)N1, sweeps, now_ms() - t0);
+  }
+}
+
+// buffers of the preconditioner and the <Kb||Ij> tensor
+void schur_init(cvsadc_ctx* c, int prec) {
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
+            L = c->naux;
+  const int64_t N1 = c->N1, nn = (int64_t)n * n;
+  cudaStream_t s = c->stream;
+  const int jc = schur_jchunk(c);
+  const int64_t v3 = (int64_t)v * v * v;
+  c->sch_h.ensure((size_t)nc * v * nc * nw * sizeof(cplx));
+  c->sch_S.ensure((size_t)N1 * N1 * sizeof(cplx));
+  c->sch_U.ensure((size_t)N1 * N1 * sizeof(cplx));
+  c->sch_V.ensure((size_t)N1 * N1 * sizeof(cplx));
+  c->sch_lam.ensure((size_t)N1 * sizeof(double));
+  c->sch_C11.ensure((size_t)nc * v * v * sizeof(cplx));
+  c->sch_C12.ensure((size_t)v * v * nc * nc * sizeof(cplx));
+  c->sch_work.ensure((size_t)(3 + nc) * jc * v3 * sizeof(cplx));
+  c->sch_tmp.ensure(std::max((size_t)v * v * nc * nc, (size_t)N1 * 64) * sizeof(cplx));
+  c->sch_th.ensure(schur_th_doubles(N1) * sizeof(double) + 256);
+  // <Kb||Ij> = (KI|bj) - (Kj|bI)
+  {
+    DBuf hc1, hc2;
+    hc1.ensure((size_t)nc * nc * v * nw * sizeof(cplx));
+    hc2.ensure((size_t)nc * nw * v * nc * sizeof(cplx));
+    const cplx* B = c->B.c();
+    gemm(c, prec, nc * nc, v * nw, L, 1.0, rows2(view(B, 0, nn), n, 1, nc),
+         cols2(view(B + (int64_t)o * n + nc, nn, 0), n, 1, nw), 0.0,
+         view(hc1.p, (int64_t)v * nw, 1));
+    gemm(c, prec, nc * nw, v * nc, L, 1.0,
+         rows2(view(B + nc, 0, nn), n, 1, nw),
+         cols2(view(B + (int64_t)o * n, nn, 0), n, 1, nc), 0.0,
+         view(hc2.p, (int64_t)v * nc, 1));
+    h_assemble(s, hc1.c(), hc2.c(), nc, nw, v, c->sch_h.c());
+    c->sync();
+  }
+}
+
+// Finds theta0 and builds the preconditioner; false when it does not apply
+// (singles space too large for the dense eigensolver, or the lowest root
+// above the lowest M22 entry).  theta0 comes from Newton's method on
+// f(theta) = lam0(S(theta)) - theta, which is concave and decreasing below
+// the lowest M22 entry, started just below it: the iterates decrease
+// monotonically towards the lowest root and stay above it.
+bool schur_setup(cvsadc_ctx* c) {
+  const double t0 = now_ms();
+  c->sch_on = false;
+  c->sch_builds = 0;
+  c->sch_couplings = 0;
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
+            L = c->naux;
+  const int64_t N1 = c->N1, N = c->N, nn = (int64_t)n * n;
+  if (N1 > 4096 || v < 2) return false;
+  const int prec = schur_precision();
+  cudaStream_t s = c->stream;
+  // lowest M22 entry
+  std::vector<double> eps(n);
+  CVS_CUDA(cudaMemcpyAsync(eps.data(), c->eps.p, n * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+  c->sync();
+  std::vector<double> ev(eps.begin() + o, eps.end());
+  std::sort(ev.begin(), ev.end());
+  const double emax_c = *std::max_element(eps.begin(), eps.begin() + nc);
+  const double emax_w = *std::max_element(eps.begin() + nc, eps.begin() + o);
+  const double pole = ev[0] + ev[1] - emax_c - emax_w;
+  schur_init(c, prec);
+  const int jc = schur_jchunk(c);
+  const int64_t v3 = (int64_t)v * v * v;
+  // keep <ab||cj> when it fits comfortably
+  size_t free_b = 0, total_b = 0;
+  CVS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  const double gbytes = (double)nw * v3 * sizeof(cplx);
+  bool cached = false;
+  if (gbytes <= std::min(0.3 * (double)free_b, 48e9)) {
+    c->sch_g.ensure((size_t)gbytes);
+    cplx* X1 = c->sch_work.c();
+    cplx* X2 = X1 + (int64_t)jc * v3;
+    for (int j0 = 0; j0 < nw; j0 += jc)
+      build_g_chunk(c, prec, j0, std::min(jc, nw - j0), X1, X2,
+                    c->sch_g.c() + (int64_t)j0 * v3);
+    cached = true;
+  }
+  // Newton on theta from just below the pole
+  DBuf xb, yb;
+  xb.ensure((size_t)N * sizeof(cplx));
+  yb.ensure((size_t)N * sizeof(cplx));
+  // start 1 Eh (or 3 % of |pole|) below the pole: when that is below the
+  // root, f > 0 and the first step moves up, never past the pole
+  const double gap = std::max(1.0, 0.03 * std::fabs(pole));
+  double theta = pole - gap;
+  double built = theta;
+  bool ok = false;
+  for (int it = 0; it < 24; ++it) {
+    build_schur(c, prec, theta, cached);
+    schur_eigh(c);
+    built = theta;
+    double lam0 = 0.0;
+    CVS_CUDA(cudaMemcpyAsync(&lam0, c->sch_lam.p, sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    c->sync();
+    if (!std::isfinite(lam0)) break;
+    if (it == 0 && lam0 >= theta && lam0 >= pole) break;  // root above the pole
+    ok = true;
+    const double f = lam0 - theta;
+    // |(theta - M22)^-1 M21 u0|^2 for the lowest eigenvector u0
+    CVS_CUDA(cudaMemsetAsync(xb.p, 0, (size_t)N * sizeof(cplx), s));
+    copyv(c, (int)N1, 1, 1.0, view(c->sch_U.c(), N1, 1), view(xb.p, 1, 1));
+    sigma_impl(c, prec, xb.c(), yb.c(), 1, SIG_FWD);
+    c->sch_couplings += 1;
+    const double wn = fold_norm(s, yb.c(), N, N1, nc, nw, v, c->eps.d(), theta,
+                                c->sch_th.d() + 128);
+    const double step = f / (-1.0 - wn);  // > 0: theta moves down
+    if (verbose())
+      fprintf(stderr, "[cvsadc] schur theta %.8f lam0 %.8f step %.3e\n", theta,
+              lam0, step);
+    if (!std::isfinite(step)) break;
+    // converged: theta0 then lies within a few hundredths of an Eh of the
+    // lowest root, which the preconditioner tolerates
+    if (std::fabs(step) < 0.05 && std::fabs(step) < 0.5 * (pole - theta)) break;
+    theta = std::min(theta - step, 0.5 * (theta + pole));
+  }
+  c->sch_theta = built;
+  c->sch_on = ok;
+  c->sync();
+  c->sch_ms = now_ms() - t0;
+  return ok;
+}
+
 // ------------------------------------------------------------- Davidson
 struct DavResult {
   int iters = 0, sigmas = 0, converged = 0;
@@ -699,7 +978,8 @@ struct DavResult {
 DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
                         int max_sub, double tol, const cplx* X0, int nx0,
                         cplx* Xout, double* wout,
-                        bool stop_on_stagnation = false) {
+                        bool stop_on_stagnation = false, bool schur = false) {
+  schur = schur && c->sch_on;
   const int64_t N = c->N;
   const int k = nroots;
   const int msub = std::max(max_sub, 2 * k + 2);
@@ -737,6 +1017,24 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     CVS_CUDA(cudaMemcpyAsync(V, X0, (size_t)nx0 * N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, s));
     nguess = nx0;
+  } else if (schur) {
+    // the lowest eigenvectors u of S(theta0) with their folded doubles
+    // (theta0 - M22)^-1 M21 u, built in W then compacted into V below
+    nguess = (int)std::min<int64_t>(std::min(nguess, 64), c->N1);
+    const int64_t N1 = c->N1;
+    CVS_CUDA(cudaMemsetAsync(W, 0, (size_t)nguess * N * sizeof(cplx), s));
+    copyv(c, nguess, (int)N1, 1.0, view(c->sch_U.c(), 1, N1), view(W, N, 1));
+    sigma_impl(c, schur_precision(), W, V, nguess, SIG_FWD);
+    c->sch_couplings += nguess;
+    std::vector<double> th0(nguess, c->sch_theta);
+    double* thd = c->sch_th.d();
+    CVS_CUDA(cudaMemcpyAsync(thd, th0.data(), nguess * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    fold_doubles(s, V, nullptr, thd, nguess, N, N1, c->ncore, c->nval,
+                 c->nvirt, c->eps.d(), false, W);
+    CVS_CUDA(cudaMemcpyAsync(V, W, (size_t)nguess * N * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, s));
+    c->sync();
   } else {
     nguess = std::min(nguess, 64);
     int64_t* idx = (int64_t*)(dwork + W_IDX);
@@ -791,6 +1089,7 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
   int m_done = 0;  // vectors whose sigma is known
   std::vector<double> theta(k), rn2(k), hist;
   std::vector<cplx> hostbuf;
+  double t_it = now_ms();
   for (int it = 0; it < max_iter; ++it) {
     // sigma for new vectors
     int nnew = m - m_done;
@@ -814,8 +1113,9 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     // Ritz vectors and their sigma images for the lowest k
     ts_combine(s, V, c->dv_U.c(), nullptr, nullptr, m, m, k, N, c->dv_X.c());
     ts_combine(s, nullptr, nullptr, W, c->dv_U.c(), m, m, k, N, c->dv_AX.c());
-    residual_precond(s, c->dv_AX.c(), c->dv_X.c(), c->dv_w.d(), c->diag.d(),
-                     k, N, c->dv_T.c(), dwork + W_PART, dwork + W_RN2);
+    residual_precond(s, c->dv_AX.c(), c->dv_X.c(), c->dv_w.d(),
+                     schur ? nullptr : c->diag.d(), k, N, c->dv_T.c(),
+                     dwork + W_PART, dwork + W_RN2);
     CVS_CUDA(cudaMemcpyAsync(theta.data(), c->dv_w.d(), k * sizeof(double),
                              cudaMemcpyDeviceToHost, s));
     CVS_CUDA(cudaMemcpyAsync(rn2.data(), dwork + W_RN2, k * sizeof(double),
@@ -832,8 +1132,9 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     if (verbose()) {
       double mx = 0;
       for (int r = 0; r < k; ++r) mx = std::max(mx, rn2[r]);
-      fprintf(stderr, "[cvsadc] davidson it %3d m %3d theta0 %.12f max|r| %.3e\n",
-              it, m, theta[0], std::sqrt(mx));
+      fprintf(stderr, "[cvsadc] davidson it %3d m %3d theta0 %.12f max|r| %.3e  t %.1f ms\n",
+              it, m, theta[0], std::sqrt(mx), now_ms() - t_it);
+      t_it = now_ms();
     }
     std::vector<int> todo;
     res.maxres = 0;
@@ -885,7 +1186,41 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
         CVS_CUDA(cudaMemcpyAsync(c->dv_T.c() + (int64_t)q * N,
                                  c->dv_T.c() + (int64_t)todo[q] * N,
                                  N * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
-    int added = orthonormalise_append(c->dv_T.c(), (int)todo.size());
+    cplx* Tn = c->dv_T.c();
+    if (schur) {
+      // block elimination with S(theta0) (see schur_setup): Z, Y are free
+      // here (the Ritz blocks are rebuilt next iteration)
+      const int cnt = (int)todo.size();
+      const int64_t N1 = c->N1;
+      const int pp = schur_precision();
+      cplx* Z = c->dv_X.c();
+      cplx* Yb = c->dv_AX.c();
+      std::vector<double> tht(cnt);
+      for (int q = 0; q < cnt; ++q) tht[q] = theta[todo[q]];
+      double* thd = c->sch_th.d();
+      CVS_CUDA(cudaMemcpyAsync(thd, tht.data(), cnt * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+      // z = (0, (theta - M22)^-1 r2);  y1 = r1 + M12 z2
+      fold_doubles(s, Tn, nullptr, thd, cnt, N, N1, c->ncore, c->nval,
+                   c->nvirt, c->eps.d(), true, Z);
+      sigma_impl(c, pp, Z, Yb, cnt, SIG_ADJ);
+      add_singles(s, Tn, Yb, N, N1, cnt, Yb);
+      // t1 = U (theta - lam)^-1 U^H y1
+      cplx* Ty = c->sch_tmp.c();
+      gemm64(c, (int)N1, cnt, (int)N1, 1.0,
+             conj_of(trans(view(c->sch_U.c(), N1, 1))), view(Yb, 1, N), 0.0,
+             view(Ty, cnt, 1));
+      eig_shift(s, Ty, N1, cnt, c->sch_lam.d(), thd);
+      gemm64(c, (int)N1, cnt, (int)N1, 1.0, view(c->sch_U.c(), N1, 1),
+             view(Ty, cnt, 1), 0.0, view(Z, 1, N));
+      // t2 = (theta - M22)^-1 (r2 + M21 t1)
+      sigma_impl(c, pp, Z, Yb, cnt, SIG_FWD);
+      fold_doubles(s, Tn, Yb, thd, cnt, N, N1, c->ncore, c->nval, c->nvirt,
+                   c->eps.d(), false, Z);
+      c->sch_couplings += 2 * cnt;
+      Tn = Z;
+    }
+    int added = orthonormalise_append(Tn, (int)todo.size());
     if (added == 0) break;
   }
   CVS_CUDA(cudaMemcpyAsync(wout, c->dv_w.d(), k * sizeof(double),
@@ -921,11 +1256,15 @@ double mixed_tolerance(int prec) {
 // the second phase.
 DavResult solve_roots(cvsadc_ctx* c, int prec, int k, double tol, int max_iter,
                       int max_sub, int refine_sweeps, bool no_refine, cplx* Xd,
-                      double* w, double* t_refine) {
+                      double* w, double* t_refine, bool use_schur = true) {
   const bool refine = needs_refine(prec) && !no_refine;
   const double tol_phase = refine ? std::max(tol, mixed_tolerance(prec)) : tol;
+  c->sch_ms = 0.0;
+  c->sch_builds = 0;
+  c->sch_couplings = 0;
+  const bool schur = use_schur && schur_setup(c);
   DavResult r = davidson_impl(c, prec, k, max_iter, max_sub, tol_phase, nullptr,
-                              0, Xd, w, needs_refine(prec));
+                              0, Xd, w, needs_refine(prec), schur);
   const double t1 = now_ms();
   if (refine) {
     DBuf X0;
@@ -934,7 +1273,7 @@ DavResult solve_roots(cvsadc_ctx* c, int prec, int k, double tol, int max_iter,
                              cudaMemcpyDeviceToDevice, c->stream));
     const int sweeps = refine_sweeps > 0 ? refine_sweeps : 20;
     DavResult r2 = davidson_impl(c, refine_precision(prec), k, sweeps, max_sub,
-                                 tol, X0.c(), k, Xd, w);
+                                 tol, X0.c(), k, Xd, w, false, schur);
     r.iters += r2.iters;
     r.sigmas += r2.sigmas;
     r.t_sigma_ms += r2.t_sigma_ms;
@@ -964,7 +1303,8 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
   DavResult r = solve_roots(c, p->precision, k, tol, max_iter, max_sub,
                             p->refine_sweeps,
                             (p->flags & CVSADC_FLAG_NO_REFINE) != 0, Xd.c(),
-                            w.data(), &t_ref);
+                            w.data(), &t_ref,
+                            (p->flags & CVSADC_FLAG_DIAG_PRECOND) == 0);
   double t1 = now_ms() - t_ref;
   phase_fix(c->stream, Xd.c(), k, c->N, c->dv_misc.d());
   if (dev)
@@ -1009,6 +1349,10 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
     info->t_sigma_ms = r.t_sigma_ms;
     info->emp2 = c->emp2;
     info->nvirt_kept = c->nvirt;
+    info->t_schur_ms = c->sch_ms;
+    info->schur_theta = c->sch_on ? c->sch_theta : 0.0;
+    info->coupling_vectors = c->sch_couplings;
+    info->schur_builds = c->sch_builds;
   }
   if (r.converged < k) throw Error{CVSADC_ENOTCONV, "Davidson did not converge"};
 }
@@ -1236,7 +1580,8 @@ void grad_entry(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   // as long as the first phase
   DavResult r = solve_roots(c, p->precision, k, tol, max_iter, max_sub,
                             p->refine_sweeps > 0 ? p->refine_sweeps : max_iter,
-                            false, Xd.c(), w.data(), nullptr);
+                            false, Xd.c(), w.data(), nullptr,
+                            (p->flags & CVSADC_FLAG_DIAG_PRECOND) == 0);
   CVS_REQUIRE(r.converged == k, CVSADC_ENOTCONV, "Davidson did not converge");
   // selected roots, contiguous
   std::vector<int> sel;
@@ -1319,9 +1664,11 @@ double estimate_bytes(const cvsadc_params* p) {
   b += z * N * (2.0 * ms + 2.0 * nkeep + k);  // Davidson V, W, X, AX, T
   b += z * (double)ms * ms * 320 + 1e6;     // subspace matrices, partials
   b += 3 * z * N;                           // moments
-  if (p->precision != CVSADC_FP64) {
+  const bool schur_on = N1 <= 4096 && !(p->flags & CVSADC_FLAG_DIAG_PRECOND);
+  if (p->precision != CVSADC_FP64 || schur_on) {
     const int ns = p->precision == CVSADC_MIXED_SLICE4 ? 4
-                   : p->precision == CVSADC_FP64_SLICE7 ? 7 : 0;
+                   : p->precision == CVSADC_FP64_SLICE7 ? 7
+                   : p->precision == CVSADC_FP64 ? 4 : 0;
     auto ws = [&](double M, double Nn, double K, int nsl) {
       if (M < 32 || K < 64 || M * Nn * K < 1e7) return 0.0;
       return (double)(nsl ? slice_workspace_bytes((int)M, (int)Nn, (int)K, nsl)
@@ -1333,6 +1680,15 @@ double estimate_bytes(const cvsadc_params* p) {
                      ws(g * N1, L, wv, ns), ws(g * wv, L, N1, ns), ws(g * N1, wv, L, ns),
                      ws(N1, g * wv, L, ns)})
       w = std::max(w, s);
+    // the preconditioner's contractions run as 4-slice products
+    if (schur_on) {
+      const double v3 = v * v * v;
+      const double jc = std::max(1.0, std::min(nw, std::floor(6e9 / ((3.0 + nc) * v3 * z))));
+      for (double s : {ws(v * v, jc * v, L, 4), ws(jc * v, v * v, L, 4),
+                       ws(nc * v, v, jc * v * v, 4), ws(g * N1, L, wv, 4),
+                       ws(g * wv, L, N1, 4), ws(g * N1, wv, L, 4), ws(N1, g * wv, L, 4)})
+        w = std::max(w, s);
+    }
     // a mixed precision is refined with the 7-slice product
     if (needs_refine(p->precision))
       for (double s : {ws(k * N1, L, wv, 7), ws(k * wv, L, N1, 7), ws(k * N1, wv, L, 7),
@@ -1341,6 +1697,17 @@ double estimate_bytes(const cvsadc_params* p) {
     b += w;
   }
   b += (double)(8 << 20) * z + 1024;        // split-K scratch, error flag
+  // Schur-complement preconditioner (when the singles space allows it)
+  if (N1 <= 4096 && !(p->flags & CVSADC_FLAG_DIAG_PRECOND)) {
+    const double v3 = v * v * v;
+    const double per_j = (3.0 + nc) * v3 * z;
+    const double jc = std::max(1.0, std::min(nw, std::floor(6e9 / per_j)));
+    b += z * (nc * v * nc * nw * 2 + nc * nc * v * nw);  // <Kb||Ij>, temps
+    b += std::min(nw * v3 * z, 48e9);          // cached <ab||cj>
+    b += 3 * z * N1 * N1 + 8 * N1 + z * nc * v * v + z * v * v * nc * nc;
+    b += (3.0 + nc) * jc * v3 * z;             // chunk workspace
+    b += z * std::max(v * v * nc * nc, N1 * 64.0) + 8 * (800 + 2 * N1) + 2 * z * N;
+  }
   return 1.1 * b + (64 << 20);
 }
 
@@ -1719,6 +2086,19 @@ int cvsadc_solve_batched(cvsadc_ctx* c, int32_t ninst, const cvsadc_params* para
   return guarded(c, [&] {
     solve_batched_impl(c, ninst, params, eps, B, dip, omega, X, osc, info, status,
                        lanes > 0 ? lanes : 4);
+  });
+}
+
+int cvsadc_get_schur(cvsadc_ctx* c, double theta, int32_t flags, void* S) {
+  if (!c || !S) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
+    c->sch_on = false;
+    schur_init(c, CVSADC_FP64);
+    build_schur(c, CVSADC_FP64, theta, false);
+    download(c, S, c->sch_S.p, (size_t)c->N1 * c->N1 * sizeof(cplx),
+             (flags & CVSADC_FLAG_DEVICE_PTRS) != 0);
+    c->sync();
   });
 }
 
