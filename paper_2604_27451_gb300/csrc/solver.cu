@@ -33,6 +33,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <complex>
 #include <condition_variable>
 #include <new>
 #include <string>
@@ -719,6 +720,9 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
 // This is a preconditioner only: its arithmetic (the tensor-core precision
 // where available) leaves the converged roots unchanged.
 
+// eigenvectors of S(theta) kept for the projected theta0 search
+constexpr int SCHUR_P = 16;
+
 // the preconditioner's GEMM precision
 int schur_precision() {
   return tc_available() ? CVSADC_MIXED_SLICE4 : CVSADC_FP64;
@@ -835,6 +839,55 @@ void schur_eigh(cvsadc_ctx* c) {
   }
 }
 
+// Lowest eigenpair of a small Hermitian matrix (host, cyclic Jacobi);
+// A is p x p row-major and is overwritten.
+double small_eigh_lowest(std::vector<std::complex<double>>& A, int p,
+                         std::vector<std::complex<double>>& y) {
+  using C = std::complex<double>;
+  std::vector<C> V((size_t)p * p, C(0, 0));
+  for (int i = 0; i < p; ++i) V[(size_t)i * p + i] = C(1, 0);
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < p; ++i)
+      for (int j = 0; j < p; ++j) {
+        const double m = std::norm(A[(size_t)i * p + j]);
+        tot += m;
+        if (i != j) off += m;
+      }
+    if (tot == 0.0 || off <= 1e-30 * tot) break;
+    for (int a = 0; a < p; ++a)
+      for (int b = a + 1; b < p; ++b) {
+        const C apq = A[(size_t)a * p + b];
+        const double r = std::abs(apq);
+        if (r == 0.0) continue;
+        const double app = A[(size_t)a * p + a].real(), aqq = A[(size_t)b * p + b].real();
+        const double tau = (aqq - app) / (2.0 * r);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t);
+        const C se = (t * cs) * (apq / r);
+        for (int k = 0; k < p; ++k) {  // rows: A <- J^H A
+          const C x = A[(size_t)a * p + k], z = A[(size_t)b * p + k];
+          A[(size_t)a * p + k] = cs * x - se * z;
+          A[(size_t)b * p + k] = std::conj(se) * x + cs * z;
+        }
+        for (int k = 0; k < p; ++k) {  // columns: A <- A J, V <- V J
+          const C x = A[(size_t)k * p + a], z = A[(size_t)k * p + b];
+          A[(size_t)k * p + a] = cs * x - std::conj(se) * z;
+          A[(size_t)k * p + b] = se * x + cs * z;
+          const C vx = V[(size_t)k * p + a], vz = V[(size_t)k * p + b];
+          V[(size_t)k * p + a] = cs * vx - std::conj(se) * vz;
+          V[(size_t)k * p + b] = se * vx + cs * vz;
+        }
+      }
+  }
+  int best = 0;
+  for (int i = 1; i < p; ++i)
+    if (A[(size_t)i * p + i].real() < A[(size_t)best * p + best].real()) best = i;
+  y.resize(p);
+  for (int k = 0; k < p; ++k) y[k] = V[(size_t)k * p + best];
+  return A[(size_t)best * p + best].real();
+}
+
 // buffers of the preconditioner and the <Kb||Ij> tensor
 void schur_init(cvsadc_ctx* c, int prec) {
   const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
@@ -915,17 +968,26 @@ bool schur_setup(cvsadc_ctx* c) {
                     c->sch_g.c() + (int64_t)j0 * v3);
     cached = true;
   }
-  // Newton on theta from just below the pole
-  DBuf xb, yb;
-  xb.ensure((size_t)N * sizeof(cplx));
-  yb.ensure((size_t)N * sizeof(cplx));
-  // start 1 Eh (or 3 % of |pole|) below the pole: when that is below the
-  // root, f > 0 and the first step moves up, never past the pole
+  // theta0: after each full build of S(theta), Newton's method runs on
+  // lam0 of S projected on its p lowest eigenvectors u_i, where for any
+  // theta only the small matrix
+  //   S_p(theta) = U^H M11 U + W^H (theta - M22)^-1 W,  W = M21 U,
+  // is needed (Rayleigh-Ritz: the projected root is never below the true
+  // one).  The next full build is at the projected root; the search ends
+  // when a build barely moves it.
+  const int pp = (int)std::min<int64_t>(SCHUR_P, N1);
+  DBuf xb, wb, zb, gb;
+  xb.ensure((size_t)pp * N * sizeof(cplx));
+  wb.ensure((size_t)pp * N * sizeof(cplx));
+  zb.ensure((size_t)pp * N * sizeof(cplx));
+  gb.ensure((size_t)(2 * pp * pp + N1 * pp) * sizeof(cplx));
+  // start 1 Eh (or 3 % of |pole|) below the pole
   const double gap = std::max(1.0, 0.03 * std::fabs(pole));
   double theta = pole - gap;
   double built = theta;
   bool ok = false;
-  for (int it = 0; it < 24; ++it) {
+  std::vector<double> thv(pp);
+  for (int it = 0; it < 6; ++it) {
     build_schur(c, prec, theta, cached);
     schur_eigh(c);
     built = theta;
@@ -934,25 +996,69 @@ bool schur_setup(cvsadc_ctx* c) {
                              cudaMemcpyDeviceToHost, s));
     c->sync();
     if (!std::isfinite(lam0)) break;
-    if (it == 0 && lam0 >= theta && lam0 >= pole) break;  // root above the pole
+    if (it == 0 && lam0 >= pole) break;  // lowest root above the pole
     ok = true;
-    const double f = lam0 - theta;
-    // |(theta - M22)^-1 M21 u0|^2 for the lowest eigenvector u0
-    CVS_CUDA(cudaMemsetAsync(xb.p, 0, (size_t)N * sizeof(cplx), s));
-    copyv(c, (int)N1, 1, 1.0, view(c->sch_U.c(), N1, 1), view(xb.p, 1, 1));
-    sigma_impl(c, prec, xb.c(), yb.c(), 1, SIG_FWD);
-    c->sch_couplings += 1;
-    const double wn = fold_norm(s, yb.c(), N, N1, nc, nw, v, c->eps.d(), theta,
-                                c->sch_th.d() + 128);
-    const double step = f / (-1.0 - wn);  // > 0: theta moves down
+    // W = M21 U_p and A_p = U_p^H M11 U_p
+    CVS_CUDA(cudaMemsetAsync(xb.p, 0, (size_t)pp * N * sizeof(cplx), s));
+    copyv(c, pp, (int)N1, 1.0, view(c->sch_U.c(), 1, N1), view(xb.p, N, 1));
+    sigma_impl(c, prec, xb.c(), wb.c(), pp, SIG_FWD);
+    c->sch_couplings += pp;
+    cplx* Gw = gb.c();
+    cplx* G2 = Gw + (int64_t)pp * pp;
+    cplx* T = G2 + (int64_t)pp * pp;
+    gemm64(c, (int)N1, pp, (int)N1, 1.0, view(c->M11.c(), N1, 1),
+           view(xb.p, 1, N), 0.0, view(T, pp, 1));
+    gemm64(c, pp, pp, (int)N1, 1.0, conj_of(view(xb.p, N, 1)), view(T, pp, 1), 0.0,
+           view(Gw, pp, 1));
+    std::vector<std::complex<double>> Ap((size_t)pp * pp), Gh((size_t)pp * pp),
+        G2h((size_t)pp * pp), Sp, y;
+    CVS_CUDA(cudaMemcpyAsync(Ap.data(), Gw, (size_t)pp * pp * sizeof(cplx),
+                             cudaMemcpyDeviceToHost, s));
+    c->sync();
+    double th = theta;
+    for (int nt = 0; nt < 40; ++nt) {
+      // Z = (th - M22)^-1 W;  G = Z^H W, G2 = Z^H Z over the doubles
+      std::fill(thv.begin(), thv.end(), th);
+      CVS_CUDA(cudaMemcpyAsync(c->sch_th.p, thv.data(), pp * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+      fold_doubles(s, wb.c(), nullptr, c->sch_th.d(), pp, N, N1, nc, nw, v,
+                   c->eps.d(), true, zb.c());
+      // rows i of conj(Z) (stride N), columns j of W and Z (stride N)
+      gemm64(c, pp, pp, (int)(N - N1), 1.0, conj_of(view(zb.c() + N1, N, 1)),
+             view(wb.c() + N1, 1, N), 0.0, view(Gw, pp, 1));
+      gemm64(c, pp, pp, (int)(N - N1), 1.0, conj_of(view(zb.c() + N1, N, 1)),
+             view(zb.c() + N1, 1, N), 0.0, view(G2, pp, 1));
+      CVS_CUDA(cudaMemcpyAsync(Gh.data(), Gw, (size_t)pp * pp * sizeof(cplx),
+                               cudaMemcpyDeviceToHost, s));
+      CVS_CUDA(cudaMemcpyAsync(G2h.data(), G2, (size_t)pp * pp * sizeof(cplx),
+                               cudaMemcpyDeviceToHost, s));
+      c->sync();
+      Sp.resize((size_t)pp * pp);
+      for (int i = 0; i < pp; ++i)
+        for (int j = 0; j < pp; ++j) {
+          const std::complex<double> a = Ap[(size_t)i * pp + j] + Gh[(size_t)i * pp + j];
+          const std::complex<double> b = Ap[(size_t)j * pp + i] + Gh[(size_t)j * pp + i];
+          Sp[(size_t)i * pp + j] = 0.5 * (a + std::conj(b));
+        }
+      const double lp = small_eigh_lowest(Sp, pp, y);
+      double zz = 0.0;  // y^H G2 y
+      for (int i = 0; i < pp; ++i) {
+        std::complex<double> t(0, 0);
+        for (int j = 0; j < pp; ++j) t += G2h[(size_t)i * pp + j] * y[j];
+        zz += (std::conj(y[i]) * t).real();
+      }
+      const double step = (lp - th) / (-1.0 - zz);
+      if (!std::isfinite(step)) break;
+      th = std::min(th - step, 0.5 * (th + pole));
+      if (std::fabs(step) < 1e-9 * std::max(1.0, std::fabs(th))) break;
+    }
     if (verbose())
-      fprintf(stderr, "[cvsadc] schur theta %.8f lam0 %.8f step %.3e\n", theta,
-              lam0, step);
-    if (!std::isfinite(step)) break;
-    // converged: theta0 then lies within a few hundredths of an Eh of the
-    // lowest root, which the preconditioner tolerates
-    if (std::fabs(step) < 0.05 && std::fabs(step) < 0.5 * (pole - theta)) break;
-    theta = std::min(theta - step, 0.5 * (theta + pole));
+      fprintf(stderr, "[cvsadc] schur theta %.8f lam0 %.8f projected root %.8f\n",
+              theta, lam0, th);
+    if (!std::isfinite(th)) break;
+    const double move = theta - th;
+    theta = th;
+    if (std::fabs(move) < 0.05) break;
   }
   c->sch_theta = built;
   c->sch_on = ok;
@@ -1650,7 +1756,9 @@ double estimate_bytes(const cvsadc_params* p) {
                                                 : std::max(8 * k, 48), 128);
   const int ms = std::max(msub, 2 * k + 2);
   const int nkeep = std::max(k, std::min(ms / 3, ms - 2 * k));
-  const double g = std::min(64, std::max(k, std::min(2 * k, ms / 2)));
+  const bool schur_on = N1 <= 4096 && !(p->flags & CVSADC_FLAG_DIAG_PRECOND);
+  double g = std::min(64, std::max(k, std::min(2 * k, ms / 2)));
+  if (schur_on) g = std::max(g, std::min<double>(SCHUR_P, N1));
   double b = 8 * n + z * L * n * n;
   b += 3 * z * n * n;                       // dipoles
   b += 2 * z * o * o * v * v;               // t2, <ab||ij>
@@ -1664,7 +1772,6 @@ double estimate_bytes(const cvsadc_params* p) {
   b += z * N * (2.0 * ms + 2.0 * nkeep + k);  // Davidson V, W, X, AX, T
   b += z * (double)ms * ms * 320 + 1e6;     // subspace matrices, partials
   b += 3 * z * N;                           // moments
-  const bool schur_on = N1 <= 4096 && !(p->flags & CVSADC_FLAG_DIAG_PRECOND);
   if (p->precision != CVSADC_FP64 || schur_on) {
     const int ns = p->precision == CVSADC_MIXED_SLICE4 ? 4
                    : p->precision == CVSADC_FP64_SLICE7 ? 7
