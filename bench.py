@@ -298,7 +298,7 @@ def run_ours(args):
         "clocks": clk.summary(), "roofline": roofline,
     }
     if rank == 0 and not args.core_only:
-        out.update(extras(args, ctx, inst, X, S, stream, torch, pkg))
+        out.update(extras(args, ctx, inst, X, S, stream, torch, pkg, (eps, B, dip)))
     elif rank == 0:
         out["e2e"] = None
     if rank == 0:
@@ -310,7 +310,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def extras(args, ctx, inst, X, S, stream, torch, pkg):
+def extras(args, ctx, inst, X, S, stream, torch, pkg, dev_inputs):
     res = {}
     # sigma builds/s of every precision on the same block
     rates = {}
@@ -343,30 +343,55 @@ def extras(args, ctx, inst, X, S, stream, torch, pkg):
     res["e2e"] = {"value": round(NVEC / dt, 3), "unit": UNIT, "h2d_bytes_per_step": nb,
                   "d2h_bytes_per_step": nb,
                   "path": "cvsadc_sigma through the C ABI with pinned host buffers"}
-    # time-to-roots, mixed vs FP64, on the small workload (full solves)
-    w = WORKLOADS["small"]
-    sm = make_instance(w["ncore"], w["nval"], w["nvirt"], w["naux"], seed=0)
-    dev = X.device
-    e_, B_, d_ = (torch.from_numpy(a).to(dev) for a in (sm.eps, sm.B, sm.dip))
-    ttr = {"workload": "small CVS-ADC(2): ncore 6, nval 14, nvirt 40, naux 240, 4 roots, "
-                       "residual 1e-7, inputs resident"}
-    roots = {}
-    for p in ("slice4", "fp64_slice7", "fp64"):
+    # time-to-roots: full solves (prepare + Davidson + refinement) with
+    # inputs resident, mixed vs FP64; the Schur-complement preconditioner
+    # is on unless the entry says "diag"
+    def solve_entry(e_, B_, d_, w, p, precond="schur", conv=1e-7):
         c2 = pkg.Context(dev.index, stream=stream.cuda_stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         o = c2.solve(e_, B_, d_, w["ncore"], w["nval"], w["nvirt"], w["nroots"],
-                     precision=p, conv=1e-7)
+                     precision=p, conv=conv, precond=precond)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        roots[p] = o["omega"].cpu().numpy()
-        ttr[p] = {"s": round(dt, 3), "status": int(o["status"]),
-                  "iterations": o["info"]["iterations"], "sigma_vectors": o["info"]["sigma_vectors"]}
         c2.close()
+        i = o["info"]
+        return o["omega"].cpu().numpy(), {
+            "s": round(dt, 3), "status": int(o["status"]), "iterations": i["iterations"],
+            "sigma_vectors": i["sigma_vectors"], "coupling_vectors": i["coupling_vectors"],
+            "schur_builds": i["schur_builds"], "t_schur_s": round(i["t_schur_ms"] / 1e3, 3),
+            "t_prepare_s": round(i["t_prepare_ms"] / 1e3, 3)}
+
+    dev = X.device
+    w = WORKLOADS["small"]
+    sm = make_instance(w["ncore"], w["nval"], w["nvirt"], w["naux"], seed=0)
+    e_, B_, d_ = (torch.from_numpy(a).to(dev) for a in (sm.eps, sm.B, sm.dip))
+    ttr = {"workload": "small CVS-ADC(2): ncore 6, nval 14, nvirt 40, naux 240, 4 roots, "
+                       "residual 1e-7, inputs resident"}
+    roots = {}
+    for p, pc in (("slice4", "schur"), ("fp64_slice7", "schur"), ("fp64", "schur"),
+                  ("fp64", "diag")):
+        key = p if pc == "schur" else p + "_diag_precond"
+        roots[key], ttr[key] = solve_entry(e_, B_, d_, w, p, pc)
     ttr["max_abs_root_diff_mixed_vs_fp64_Eh"] = float(np.abs(roots["slice4"] - roots["fp64"]).max())
     ttr["max_abs_root_diff_fp64_slice7_vs_fp64_Eh"] = float(np.abs(roots["fp64_slice7"] - roots["fp64"]).max())
     ttr["speedup_mixed_vs_fp64"] = round(ttr["fp64"]["s"] / ttr["slice4"]["s"], 2)
     res["time_to_roots"] = ttr
+    # the medium workload (the one the sigma rate is quoted on)
+    wm = WORKLOADS[WORKLOAD]
+    ttm = {"workload": "medium CVS-ADC(2): ncore %d, nval %d, nvirt %d, naux %d, %d roots, "
+                       "residual 1e-6, inputs resident" % (
+                           wm["ncore"], wm["nval"], wm["nvirt"], wm["naux"], wm["nroots"])}
+    rm = {}
+    rm["slice4"], ttm["slice4"] = solve_entry(dev_inputs[0], dev_inputs[1], dev_inputs[2], wm,
+                                              "slice4", conv=1e-6)
+    if args.ttr_medium_fp64:
+        rm["fp64"], ttm["fp64"] = solve_entry(dev_inputs[0], dev_inputs[1], dev_inputs[2], wm,
+                                              "fp64", conv=1e-6)
+        ttm["max_abs_root_diff_mixed_vs_fp64_Eh"] = float(np.abs(rm["slice4"] - rm["fp64"]).max())
+        ttm["speedup_mixed_vs_fp64"] = round(ttm["fp64"]["s"] / ttm["slice4"]["s"], 2)
+    ttm["roots_Eh"] = [round(float(x), 9) for x in rm["slice4"]]
+    res["time_to_roots_medium"] = ttm
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
     return res
@@ -432,6 +457,8 @@ def main():
                     help="only the timed sigma steps (used for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ttr-medium-fp64", action="store_true",
+                    help="also time the FP64 solve of the medium workload (minutes)")
     ap.add_argument("--profile-gemm", action="store_true",
                     help="run one 4096^3 complex GEMM three times (ncu case)")
     args = ap.parse_args()

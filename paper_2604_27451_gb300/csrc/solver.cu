@@ -1261,6 +1261,11 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
       if (res.maxres < 100 * tol && hist.size() > 30 &&
           res.maxres > 0.5 * hist[hist.size() - 31])
         break;
+      // with the Schur preconditioner the residual falls several-fold per
+      // iteration until the noise floor: hand over once three iterations
+      // have not halved it
+      if (schur && hist.size() > 3 && res.maxres > 0.5 * hist[hist.size() - 4])
+        break;
     }
     // thick restart to the nkeep lowest Ritz vectors when the block does
     // not fit
