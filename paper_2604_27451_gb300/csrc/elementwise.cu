@@ -177,8 +177,13 @@ __global__ void unpack_kernel(const cplx* __restrict__ x2, int nc, int nw,
 }
 
 // one block per (I, j, a) row of the packed doubles
+// sigma2 = -(G_{Ia,jb} - G_{Ib,ja}) + sum_K (x_Ka h_KbIj - x_Kb h_KaIj)
+//          + M22 x2, packed over a < b (x2 may be NULL: no M22 term; h may be
+// NULL: no h term); h[K][b][I][j] = <Kb||Ij>, x1 the singles [K][a]
 __global__ void sigma2_kernel(const cplx* __restrict__ G,
                               const cplx* __restrict__ x2,
+                              const cplx* __restrict__ x1,
+                              const cplx* __restrict__ h,
                               const double* __restrict__ eps, int nc, int nw,
                               int nv, cplx* __restrict__ s2) {
   const int64_t npair = (int64_t)nv * (nv - 1) / 2;
@@ -197,6 +202,16 @@ __global__ void sigma2_kernel(const cplx* __restrict__ G,
       cplx g2 = G[(((int64_t)I * nv + b) * nw + j) * nv + a];
       int64_t d = base + b;
       cplx out = csub(g2, g1);
+      if (h) {
+        const int64_t hs = (int64_t)nv * nc * nw;  // stride of K in h
+        const int64_t hb = (int64_t)I * nw + j;
+        for (int K = 0; K < nc; ++K) {
+          const cplx xa = x1[(int64_t)K * nv + a], xb = x1[(int64_t)K * nv + b];
+          const cplx hkb = h[K * hs + (int64_t)b * nc * nw + hb];
+          const cplx hka = h[K * hs + (int64_t)a * nc * nw + hb];
+          out = cadd(out, csub(cmul(xa, hkb), cmul(xb, hka)));
+        }
+      }
       if (x2) {  // without x2: the coupling M21 x1 alone
         cplx x = x2[d];
         double m22 = e0 + eps[o + b];
@@ -710,12 +725,36 @@ void unpack_doubles(cudaStream_t s, const cplx* x2, int ncore, int nval,
   CVS_CHECK_LAUNCH();
 }
 
+namespace {
+// hT[((I nw + j) nv + b) nc + K] = conj(h[K][b][I][j])
+__global__ void h_conj_t_kernel(const cplx* __restrict__ h, int nc, int nw,
+                                int nv, cplx* __restrict__ hT) {
+  const int64_t total = (int64_t)nc * nw * nv * nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int K = e % nc;
+    int64_t r = e / nc;
+    const int b = r % nv;
+    r /= nv;
+    const int j = r % nw, I = r / nw;
+    hT[e] = cconj(h[(((int64_t)K * nv + b) * nc + I) * nw + j]);
+  }
+}
+}  // namespace
+
+void h_conj_transpose(cudaStream_t s, const cplx* h, int nc, int nw, int nv,
+                      cplx* hT) {
+  h_conj_t_kernel<<<grid1d((int64_t)nc * nw * nv * nc, 256), 256, 0, s>>>(
+      h, nc, nw, nv, hT);
+  CVS_CHECK_LAUNCH();
+}
+
 void sigma2_finish(cudaStream_t s, const cplx* G, const cplx* x2,
-                   const double* eps, int ncore, int nval, int nvirt,
-                   cplx* s2) {
+                   const cplx* x1, const cplx* h, const double* eps, int ncore,
+                   int nval, int nvirt, cplx* s2) {
   int64_t rows = (int64_t)ncore * nval * nvirt;
   unsigned g = rows > 65535 * 8 ? 65535 * 8 : (unsigned)rows;
-  sigma2_kernel<<<g, 128, 0, s>>>(G, x2, eps, ncore, nval, nvirt, s2);
+  sigma2_kernel<<<g, 128, 0, s>>>(G, x2, x1, h, eps, ncore, nval, nvirt, s2);
   CVS_CHECK_LAUNCH();
 }
 

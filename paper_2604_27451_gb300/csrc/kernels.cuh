@@ -67,8 +67,10 @@ void unpack_doubles(cudaStream_t s, const cplx* x2, int ncore, int nval,
                     int nvirt, cplx* Yt);
 // sigma2[d] = -(G[I,a,j,b] - G[I,b,j,a]) + (e_a+e_b-e_I-e_j) x2[d]
 void sigma2_finish(cudaStream_t s, const cplx* G, const cplx* x2,
-                   const double* eps, int ncore, int nval, int nvirt,
-                   cplx* s2);
+                   const cplx* x1, const cplx* h, const double* eps, int ncore,
+                   int nval, int nvirt, cplx* s2);
+void h_conj_transpose(cudaStream_t s, const cplx* h, int nc, int nw, int nv,
+                      cplx* hT);
 // pack an antisymmetric-by-construction full tensor F[I][j][a][b] with
 // F = -(A[a][b] - A[b][a]) + T[a][b] into packed doubles (a < b).
 void pack_moment_doubles(cudaStream_t s, const cplx* A, const cplx* T,

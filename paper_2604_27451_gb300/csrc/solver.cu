@@ -155,6 +155,8 @@ struct cvsadc_ctx {
   bool has_dip = false, has_fns = false;
   double emp2 = 0.0;
   DBuf eps, B, dip, t2, g2, M11, diag, F, fns_occ, fns_U;
+  // <Kb||Ij> as h[K][b][I][j], and conj(h) as hT[(I,j,b)][K]
+  DBuf h1, hT;
 
   // scratch
   DBuf s_big1, s_big2, s_S, s_R, s_Y, s_V, s_part, s_small, s_tc;
@@ -163,7 +165,7 @@ struct cvsadc_ctx {
   DBuf s_kpart;  // split-K partial products
 
   // Schur-complement preconditioner of the prepared problem
-  DBuf sch_h, sch_g, sch_S, sch_U, sch_V, sch_lam, sch_C11, sch_C12, sch_work,
+  DBuf sch_g, sch_S, sch_U, sch_V, sch_lam, sch_C11, sch_C12, sch_work,
       sch_tmp, sch_th;
   bool sch_on = false;
   double sch_theta = 0.0, sch_ms = 0.0;
@@ -174,10 +176,10 @@ struct cvsadc_ctx {
 
   void sync() { CVS_CUDA(cudaStreamSynchronize(stream)); }
   std::vector<DBuf*> problem_buffers() {
-    return {&eps,   &B,     &dip,   &t2,   &g2,     &M11,  &diag, &F,
+    return {&eps,   &B,     &dip,   &t2,   &g2,     &M11,  &diag, &F, &h1, &hT,
             &fns_occ, &fns_U, &s_big1, &s_big2, &s_S, &s_R, &s_Y, &s_V,
             &s_part, &s_small, &s_tc, &dv_V, &dv_W, &dv_X, &dv_AX, &dv_T,
-            &dv_H,  &dv_A,  &dv_U,  &dv_w, &dv_misc, &sch_h, &sch_g,
+            &dv_H,  &dv_A,  &dv_U,  &dv_w, &dv_misc, &sch_g,
             &sch_S, &sch_U, &sch_V, &sch_lam, &sch_C11, &sch_C12, &sch_work,
             &sch_tmp, &sch_th};
   }
@@ -416,6 +418,35 @@ void build_moments(cvsadc_ctx* c, int prec) {
   }
 }
 
+// ------------------------------------------------- <Kb||Ij> (1-external)
+// h[K][b][I][j] = <Kb||Ij> = (KI|bj) - (Kj|bI), and its conjugate laid out
+// as hT[(I,j,b)][K].  Small (ncore^2 nval nvirt) and kept with the
+// prepared problem: the couplings' terms with one virtual index go through
+// it, the ones with three (<ab||cj>) through B^P.
+void build_h(cvsadc_ctx* c, int prec) {
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
+            L = c->naux;
+  const int64_t nn = (int64_t)n * n;
+  cudaStream_t s = c->stream;
+  c->h1.ensure((size_t)nc * v * nc * nw * sizeof(cplx));
+  c->hT.ensure((size_t)nc * v * nc * nw * sizeof(cplx));
+  DBuf hc1, hc2;
+  hc1.ensure((size_t)nc * nc * v * nw * sizeof(cplx));
+  hc2.ensure((size_t)nc * nw * v * nc * sizeof(cplx));
+  const cplx* B = c->B.c();
+  // hc1[(K,I)][(b,j)] = sum_P B^P_KI B^P_bj
+  gemm(c, prec, nc * nc, v * nw, L, 1.0, rows2(view(B, 0, nn), n, 1, nc),
+       cols2(view(B + (int64_t)o * n + nc, nn, 0), n, 1, nw), 0.0,
+       view(hc1.p, (int64_t)v * nw, 1));
+  // hc2[(K,j)][(b,I)] = sum_P B^P_Kj B^P_bI
+  gemm(c, prec, nc * nw, v * nc, L, 1.0, rows2(view(B + nc, 0, nn), n, 1, nw),
+       cols2(view(B + (int64_t)o * n, nn, 0), n, 1, nc), 0.0,
+       view(hc2.p, (int64_t)v * nc, 1));
+  h_assemble(s, hc1.c(), hc2.c(), nc, nw, v, c->h1.c());
+  h_conj_transpose(s, c->h1.c(), nc, nw, v, c->hT.c());
+  c->sync();
+}
+
 // ----------------------------------------------------------------- sigma
 // sigma for a group of g vectors at once: every contraction runs over the
 // whole group, so the ncore-sized dimensions become g * ncore and operands
@@ -429,68 +460,49 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
   const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
             L = c->naux;
   const int64_t nn = (int64_t)n * n, N1 = c->N1, N = c->N;
-  const int64_t wv = (int64_t)nw * v, vL = (int64_t)v * L, wvL = wv * L;
+  const int64_t wv = (int64_t)nw * v, vL = (int64_t)v * L;
   const int64_t N1L = N1 * L, N1wv = N1 * wv;
   const cplx* B = c->B.c();
   c->s_big1.ensure((size_t)g * N1wv * sizeof(cplx));
   c->s_big2.ensure((size_t)g * N1wv * sizeof(cplx));
   c->s_S.ensure((size_t)g * N1L * sizeof(cplx));
-  c->s_R.ensure((size_t)g * wvL * sizeof(cplx));
   c->s_Y.ensure((size_t)g * N1L * sizeof(cplx));
-  c->s_V.ensure((size_t)g * wvL * sizeof(cplx));
   cplx* Yt = c->s_big1.c();  // [q][I][a][j][b]
   cplx* G = c->s_big2.c();   // [q][(I,a)][(j,b)]
   cplx* S = c->s_S.c();      // [(q,I,a)][P]
-  cplx* R = c->s_R.c();      // [(q,c,j)][P]
   cplx* Y = c->s_Y.c();      // [(q,I,a)][P]
-  cplx* Vv = c->s_V.c();     // [(q,j,b)][P]
   if (mode != SIG_FWD) {
-  for (int q = 0; q < g; ++q)
-    unpack_doubles(c->stream, x + q * N + N1, nc, nw, v, Yt + q * N1wv);
-  // S[(q,I,a)][P] = sum_{jb} y_{Ijab} B^P_{jb}
-  gemm(c, prec, (int)(g * N1), L, (int)wv, 1.0, view(Yt, wv, 1),
-       rows2(view(B + (int64_t)nc * n + o, 0, nn), n, 1, v), 0.0,
-       view(S, L, 1));
-  // R[(q,c,j)][P] = sum_{Ib} y_{Ijcb} B^P_{Ib}
-  gemm(c, prec, (int)(g * wv), L, (int)N1,
-       1.0, cols2(rows2(view(Yt, 0, 0), N1wv, v, (int)wv), wv * v, 1, v),
-       rows2(view(B + o, 0, nn), n, 1, v), 0.0, view(R, L, 1));
-  // sigma1 (M12 x2): rows (q, K), columns c
-  const View s1rows = rows2(view(sig, 0, 1), N, v, nc);
-  gemm(c, prec, g * nc, v, (int)vL, -1.0, view(S, vL, 1),
-       rows2(view(B + (int64_t)o * n + o, 0, n), 1, nn, L), 0.0, s1rows);
-  // the two contractions with the core index K as output column: rows
-  // (q, c) so that the long dimension is the GEMM's M
-  const View s1t = rows2(view(sig, 0, v), N, 1, v);  // ((q,c), K)
-  gemm(c, prec, g * v, nc, nc * L, 1.0,
-       cols2(rows2(view(S, 0, 0), N1L, L, v), vL, 1, L),
-       rows2(view(B, 0, 1), n, nn, L), 1.0, s1t);
-  gemm(c, prec, g * v, nc, nw * L, -1.0, view(R, (int64_t)nw * L, 1),
-       rows2(view(B + (int64_t)nc * n, 0, 1), n, nn, L), 1.0, s1t);
+    for (int q = 0; q < g; ++q)
+      unpack_doubles(c->stream, x + q * N + N1, nc, nw, v, Yt + q * N1wv);
+    // S[(q,I,a)][P] = sum_{jb} y_{Ijab} B^P_{jb}
+    gemm(c, prec, (int)(g * N1), L, (int)wv, 1.0, view(Yt, wv, 1),
+         rows2(view(B + (int64_t)nc * n + o, 0, nn), n, 1, v), 0.0,
+         view(S, L, 1));
+    // sigma1 (M12 x2), the <ab||cj> part: rows (q, K), columns c
+    const View s1rows = rows2(view(sig, 0, 1), N, v, nc);
+    gemm(c, prec, g * nc, v, (int)vL, -1.0, view(S, vL, 1),
+         rows2(view(B + (int64_t)o * n + o, 0, n), 1, nn, L), 0.0, s1rows);
+    // the <Kb||Ij> part: sigma1[K][c] += sum_{Ijb} y_{Ijcb} conj(h[K][b][I][j]),
+    // rows (q, c), columns K
+    const View s1t = rows2(view(sig, 0, v), N, 1, v);  // ((q,c), K)
+    gemm(c, prec, g * v, nc, (int)(nc * wv), 1.0,
+         cols2(rows2(view(Yt, 0, 0), N1wv, wv, v), wv * v, 1, (int)wv),
+         view(c->hT.c(), nc, 1), 1.0, s1t);
   }
   if (mode == SIG_ADJ) return;
-  // Y[(q,I,a)][P] = sum_c x_Ic B^P_ac - sum_K x_Ka B^P_KI
+  // Y[(q,I,a)][P] = sum_c x_Ic B^P_ac
   gemm(c, prec, g * nc, (int)vL, v, 1.0, rows2(view(x, 0, 1), N, v, nc),
        cols2(view(B + (int64_t)o * n + o, 1, 0), n, nn, L), 0.0,
        view(Y, vL, 1));
-  gemm(c, prec, g * v, nc * L, nc, -1.0, rows2(view(x, 0, v), N, 1, v),
-       cols2(view(B, n, 0), 1, nn, L), 1.0,
-       cols2(rows2(view(Y, 0, 0), N1L, L, v), vL, 1, L));
-  // Vv[(q,j,b)][P] = sum_K x_Kb B^P_{K j}
-  gemm(c, prec, g * v, nw * L, nc, 1.0, rows2(view(x, 0, v), N, 1, v),
-       cols2(view(B + nc, n, 0), 1, nn, L), 0.0,
-       cols2(rows2(view(Vv, 0, 0), wvL, L, v), vL, 1, L));
-  // G[q][(I,a)][(j,b)] = sum_P Y B^P_{bj} - sum_P B^P_{aI} Vv
+  // G[q][(I,a)][(j,b)] = sum_P Y B^P_{bj} (the <ab||cj> part of M21 x1; the
+  // <Kb||Ij> part is added while packing)
   gemm(c, prec, (int)(g * N1), (int)wv, L, 1.0, view(Y, L, 1),
        cols2(view(B + (int64_t)o * n + nc, nn, 0), 1, n, v), 0.0,
        view(G, wv, 1));
-  gemm(c, prec, (int)N1, (int)(g * wv), L, -1.0,
-       rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v), view(Vv, 1, L), 1.0,
-       cols2(view(G, wv, 0), N1wv, 1, (int)wv));
   for (int q = 0; q < g; ++q)
     sigma2_finish(c->stream, G + q * N1wv,
-                  mode == SIG_FWD ? nullptr : x + q * N + N1, c->eps.d(), nc,
-                  nw, v, sig + q * N + N1);
+                  mode == SIG_FWD ? nullptr : x + q * N + N1, x + q * N,
+                  c->h1.c(), c->eps.d(), nc, nw, v, sig + q * N + N1);
   if (mode == SIG_FWD) return;
   // sigma1 += M11 x1 (dense product, FP64 for the small block)
   gemm64(c, (int)N1, g, (int)N1, 1.0, view(c->M11.c(), N1, 1), view(x, 1, N),
@@ -690,6 +702,7 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   stage("t2", ts);
   ts = now_ms();
   build_m11(c, prec);
+  build_h(c, prec);
   stage("m11", ts);
   ts = now_ms();
   if (c->has_dip) build_moments(c, prec);
@@ -793,7 +806,7 @@ void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached) {
     }
     // (12): C12[c'][c][K][K'] += sum_b conj(<c'b||cj>) w_{Kjc'b} <K'b||Kj>
     for (int jl = 0; jl < jn; ++jl) {
-      h_weight(s, c->sch_h.c(), j0 + jl, nc, nw, v, c->eps.d(), theta, Hw);
+      h_weight(s, c->h1.c(), j0 + jl, nc, nw, v, c->eps.d(), theta, Hw);
       gemm(c, CVSADC_FP64, v, nc * nc, v, 1.0,
            batched(conj_of(view(G + (int64_t)jl * v3, 1, v)), (int64_t)v * v),
            batched(view(Hw, nc * nc, 1), (int64_t)v * nc * nc), 1.0,
@@ -805,7 +818,7 @@ void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached) {
       tv = now_ms();
     }
   }
-  schur_assemble(s, c->M11.c(), c->sch_C11.c(), c->sch_C12.c(), c->sch_h.c(), nc,
+  schur_assemble(s, c->M11.c(), c->sch_C11.c(), c->sch_C12.c(), c->h1.c(), nc,
                  nw, v, c->eps.d(), theta, c->sch_V.c(), c->sch_S.c());
   if (vb) {
     c->sync();
@@ -896,7 +909,6 @@ void schur_init(cvsadc_ctx* c, int prec) {
   cudaStream_t s = c->stream;
   const int jc = schur_jchunk(c);
   const int64_t v3 = (int64_t)v * v * v;
-  c->sch_h.ensure((size_t)nc * v * nc * nw * sizeof(cplx));
   c->sch_S.ensure((size_t)N1 * N1 * sizeof(cplx));
   c->sch_U.ensure((size_t)N1 * N1 * sizeof(cplx));
   c->sch_V.ensure((size_t)N1 * N1 * sizeof(cplx));
@@ -906,22 +918,6 @@ void schur_init(cvsadc_ctx* c, int prec) {
   c->sch_work.ensure((size_t)(3 + nc) * jc * v3 * sizeof(cplx));
   c->sch_tmp.ensure(std::max((size_t)v * v * nc * nc, (size_t)N1 * 64) * sizeof(cplx));
   c->sch_th.ensure(schur_th_doubles(N1) * sizeof(double) + 256);
-  // <Kb||Ij> = (KI|bj) - (Kj|bI)
-  {
-    DBuf hc1, hc2;
-    hc1.ensure((size_t)nc * nc * v * nw * sizeof(cplx));
-    hc2.ensure((size_t)nc * nw * v * nc * sizeof(cplx));
-    const cplx* B = c->B.c();
-    gemm(c, prec, nc * nc, v * nw, L, 1.0, rows2(view(B, 0, nn), n, 1, nc),
-         cols2(view(B + (int64_t)o * n + nc, nn, 0), n, 1, nw), 0.0,
-         view(hc1.p, (int64_t)v * nw, 1));
-    gemm(c, prec, nc * nw, v * nc, L, 1.0,
-         rows2(view(B + nc, 0, nn), n, 1, nw),
-         cols2(view(B + (int64_t)o * n, nn, 0), n, 1, nc), 0.0,
-         view(hc2.p, (int64_t)v * nc, 1));
-    h_assemble(s, hc1.c(), hc2.c(), nc, nw, v, c->sch_h.c());
-    c->sync();
-  }
 }
 
 // Finds theta0 and builds the preconditioner; false when it does not apply
