@@ -165,7 +165,7 @@ struct cvsadc_ctx {
   DBuf s_kpart;  // split-K partial products
 
   // Schur-complement preconditioner of the prepared problem
-  DBuf sch_g, sch_S, sch_U, sch_V, sch_lam, sch_C11, sch_C12, sch_work,
+  DBuf sch_W, sch_g, sch_S, sch_U, sch_V, sch_lam, sch_C11, sch_C12, sch_work,
       sch_tmp, sch_th;
   bool sch_on = false;
   double sch_theta = 0.0, sch_ms = 0.0;
@@ -179,7 +179,7 @@ struct cvsadc_ctx {
     return {&eps,   &B,     &dip,   &t2,   &g2,     &M11,  &diag, &F, &h1, &hT,
             &fns_occ, &fns_U, &s_big1, &s_big2, &s_S, &s_R, &s_Y, &s_V,
             &s_part, &s_small, &s_tc, &dv_V, &dv_W, &dv_X, &dv_AX, &dv_T,
-            &dv_H,  &dv_A,  &dv_U,  &dv_w, &dv_misc, &sch_g,
+            &dv_H,  &dv_A,  &dv_U,  &dv_w, &dv_misc, &sch_W, &sch_g,
             &sch_S, &sch_U, &sch_V, &sch_lam, &sch_C11, &sch_C12, &sch_work,
             &sch_tmp, &sch_th};
   }
@@ -834,16 +834,38 @@ size_t schur_th_doubles(int64_t N1) {
   return 736 + ((cc_n + 1) & ~(size_t)1) + 2 * cc_n;
 }
 
-void schur_eigh(cvsadc_ctx* c) {
+// Eigen-decomposition of sch_S into sch_U / sch_lam.  With warm set,
+// sch_U holds the eigenvectors of a nearby S (the previous theta): S is
+// first transformed into that basis, where it is nearly diagonal, so the
+// Jacobi sweeps needed drop, and the eigenvectors are mapped back.
+void schur_eigh(cvsadc_ctx* c, bool warm = false) {
   const double t0 = verbose() ? (c->sync(), now_ms()) : 0.0;
   const int64_t N1 = c->N1;
   const size_t cc_n = (size_t)(N1 / 2 + 2);
   double* part = c->sch_th.d() + 128;
   double* cc = c->sch_th.d() + 736;
   cplx* se = (cplx*)(c->sch_th.d() + 736 + ((cc_n + 1) & ~(size_t)1));
+  if (warm) {
+    // sch_V = S U_prev; sch_S = U_prev^H sch_V; sch_W keeps U_prev
+    c->sch_W.ensure((size_t)N1 * N1 * sizeof(cplx));
+    CVS_CUDA(cudaMemcpyAsync(c->sch_W.p, c->sch_U.p, (size_t)N1 * N1 * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, c->stream));
+    gemm64(c, (int)N1, (int)N1, (int)N1, 1.0, view(c->sch_S.c(), N1, 1),
+           view(c->sch_W.c(), N1, 1), 0.0, view(c->sch_V.c(), N1, 1));
+    gemm64(c, (int)N1, (int)N1, (int)N1, 1.0,
+           conj_of(trans(view(c->sch_W.c(), N1, 1))), view(c->sch_V.c(), N1, 1),
+           0.0, view(c->sch_S.c(), N1, 1));
+  }
   const int sweeps =
       jacobi_eigh_parallel(c->stream, c->sch_S.c(), (int)N1, c->sch_lam.d(),
                            c->sch_U.c(), c->sch_V.c(), part, cc, se, 30);
+  if (warm) {
+    // eigenvectors in the original basis: U = U_prev U'
+    CVS_CUDA(cudaMemcpyAsync(c->sch_V.p, c->sch_U.p, (size_t)N1 * N1 * sizeof(cplx),
+                             cudaMemcpyDeviceToDevice, c->stream));
+    gemm64(c, (int)N1, (int)N1, (int)N1, 1.0, view(c->sch_W.c(), N1, 1),
+           view(c->sch_V.c(), N1, 1), 0.0, view(c->sch_U.c(), N1, 1));
+  }
   ++c->sch_builds;
   if (verbose()) {
     c->sync();
@@ -985,7 +1007,7 @@ bool schur_setup(cvsadc_ctx* c) {
   std::vector<double> thv(pp);
   for (int it = 0; it < 6; ++it) {
     build_schur(c, prec, theta, cached);
-    schur_eigh(c);
+    schur_eigh(c, it > 0);
     built = theta;
     double lam0 = 0.0;
     CVS_CUDA(cudaMemcpyAsync(&lam0, c->sch_lam.p, sizeof(double),
@@ -1812,7 +1834,7 @@ double estimate_bytes(const cvsadc_params* p) {
     const double jc = std::max(1.0, std::min(nw, std::floor(6e9 / per_j)));
     b += z * (nc * v * nc * nw * 2 + nc * nc * v * nw);  // <Kb||Ij>, temps
     b += std::min(nw * v3 * z, 48e9);          // cached <ab||cj>
-    b += 3 * z * N1 * N1 + 8 * N1 + z * nc * v * v + z * v * v * nc * nc;
+    b += 4 * z * N1 * N1 + 8 * N1 + z * nc * v * v + z * v * v * nc * nc;
     b += (3.0 + nc) * jc * v3 * z;             // chunk workspace
     b += z * std::max(v * v * nc * nc, N1 * 64.0) + 8 * (800 + 2 * N1) + 2 * z * N;
   }
