@@ -267,14 +267,68 @@ __global__ void diag_kernel(const cplx* M11, const double* eps, int nc,
 }
 
 // ---------------------------------------------------- tall-skinny kernels
+// ---- double-float arithmetic for the Davidson vector algebra
+// FP64 runs at a small fraction of the FP32 rate on this GPU, so the dot
+// products and linear combinations over N-long vectors use pairs of floats
+// (hi + lo, ~48-bit significand): each FP64 operand is split once as it is
+// loaded, a product keeps the exact rounding error of hi*hi (an FMA) plus
+// the cross terms, and the accumulator adds with TwoSum (no contraction).
+struct dfc {  // complex double-float: re = (rh, rl), im = (ih, il)
+  float rh, rl, ih, il;
+};
+
+__device__ __forceinline__ dfc to_dfc(cplx x) {
+  dfc d;
+  d.rh = __double2float_rn(x.x);
+  d.rl = __double2float_rn(x.x - (double)d.rh);
+  d.ih = __double2float_rn(x.y);
+  d.il = __double2float_rn(x.y - (double)d.ih);
+  return d;
+}
+
+// (sh, sl) += (ah + al)(bh + bl), sign s = +-1 applied to the product
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
+                                       float bh, float bl, float sg) {
+  const float p = __fmul_rn(sg * ah, bh);
+  float e = __fmaf_rn(sg * ah, bh, -p);
+  e = __fmaf_rn(sg * ah, bl, e);
+  e = __fmaf_rn(sg * al, bh, e);
+  const float t = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(t, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// acc += conj(a) * b  (acc as two (hi, lo) pairs)
+__device__ __forceinline__ void dfc_conj_mac(float* acc, const dfc& a, const dfc& b) {
+  // re += ar br + ai bi ; im += ar bi - ai br
+  df_mac(acc[0], acc[1], a.rh, a.rl, b.rh, b.rl, 1.0f);
+  df_mac(acc[0], acc[1], a.ih, a.il, b.ih, b.il, 1.0f);
+  df_mac(acc[2], acc[3], a.rh, a.rl, b.ih, b.il, 1.0f);
+  df_mac(acc[2], acc[3], a.ih, a.il, b.rh, b.rl, -1.0f);
+}
+
+// acc += a * b
+__device__ __forceinline__ void dfc_mac(float* acc, const dfc& a, const dfc& b) {
+  df_mac(acc[0], acc[1], a.rh, a.rl, b.rh, b.rl, 1.0f);
+  df_mac(acc[0], acc[1], a.ih, a.il, b.ih, b.il, -1.0f);
+  df_mac(acc[2], acc[3], a.rh, a.rl, b.ih, b.il, 1.0f);
+  df_mac(acc[2], acc[3], a.ih, a.il, b.rh, b.rl, 1.0f);
+}
+
+__device__ __forceinline__ cplx dfc_value(const float* acc) {
+  return cmake((double)acc[0] + (double)acc[1], (double)acc[2] + (double)acc[3]);
+}
+
 constexpr int TSN = 16;  // n-tile of ts_dot
 
 __global__ void ts_dot_kernel(const cplx* __restrict__ A, int ma,
                               const cplx* __restrict__ B, int mb, int64_t N,
                               cplx* __restrict__ part) {
-  extern __shared__ cplx sh[];
-  cplx* sa = sh;             // [ma][TSN]
-  cplx* sb = sh + ma * TSN;  // [mb][TSN]
+  extern __shared__ dfc shd[];
+  dfc* sa = shd;             // [ma][TSN]
+  dfc* sb = shd + ma * TSN;  // [mb][TSN]
   const int npairs = ma * mb;
   const int per = (npairs + blockDim.x - 1) / blockDim.x;  // <= 16
   double ar[16], ai[16];
@@ -288,25 +342,21 @@ __global__ void ts_dot_kernel(const cplx* __restrict__ A, int ma,
       int64_t n = t0 + k;
       cplx val = cmake(0, 0);
       if (n < n1) val = vec < ma ? A[(int64_t)vec * N + n] : B[(int64_t)(vec - ma) * N + n];
-      sh[e] = val;
+      shd[e] = to_dfc(val);
     }
     __syncthreads();
     for (int q = 0; q < per; ++q) {
       int pr = threadIdx.x + q * blockDim.x;
       if (pr >= npairs) break;
       int i = pr / mb, j = pr % mb;
-      const cplx* x = sa + i * TSN;
-      const cplx* y = sb + j * TSN;
-      double sr = 0, si = 0;
+      const dfc* x = sa + i * TSN;
+      const dfc* y = sb + j * TSN;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int k = 0; k < TSN; ++k) {
-        sr = fma(x[k].x, y[k].x, sr);
-        sr = fma(x[k].y, y[k].y, sr);
-        si = fma(x[k].x, y[k].y, si);
-        si = fma(-x[k].y, y[k].x, si);
-      }
-      ar[q] += sr;
-      ai[q] += si;
+      for (int k = 0; k < TSN; ++k) dfc_conj_mac(acc, x[k], y[k]);
+      const cplx v = dfc_value(acc);
+      ar[q] += v.x;
+      ai[q] += v.y;
     }
   }
   for (int q = 0; q < per; ++q) {
@@ -337,68 +387,61 @@ __global__ void ts_combine_kernel(const cplx* __restrict__ V,
                                   const cplx* __restrict__ W,
                                   const cplx* __restrict__ cw, int m, int ldc,
                                   int k, int64_t N, cplx* __restrict__ out) {
-  extern __shared__ cplx coef[];  // [2][m][k]
+  extern __shared__ dfc coefd[];  // [2][m][k]
   for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
     int i = e / k, r = e % k;
-    coef[e] = cv ? cv[i * ldc + r] : cmake(0, 0);
-    coef[m * k + e] = cw ? cw[i * ldc + r] : cmake(0, 0);
+    coefd[e] = to_dfc(cv ? cv[i * ldc + r] : cmake(0, 0));
+    coefd[m * k + e] = to_dfc(cw ? cw[i * ldc + r] : cmake(0, 0));
   }
   __syncthreads();
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
        n += (int64_t)gridDim.x * blockDim.x) {
     for (int r0 = 0; r0 < k; r0 += 8) {
-      double accr[8], acci[8];
+      float acc[8][4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) accr[q] = acci[q] = 0.0;
+      for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
       for (int i = 0; i < m; ++i) {
-        cplx vv = V ? V[(int64_t)i * N + n] : cmake(0, 0);
-        cplx ww = W ? W[(int64_t)i * N + n] : cmake(0, 0);
+        const dfc vv = to_dfc(V ? V[(int64_t)i * N + n] : cmake(0, 0));
+        const dfc ww = to_dfc(W ? W[(int64_t)i * N + n] : cmake(0, 0));
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           int r = r0 + q;
           if (r < k) {
-            cplx a = coef[i * k + r];
-            cplx b = coef[m * k + i * k + r];
-            accr[q] += vv.x * a.x - vv.y * a.y + ww.x * b.x - ww.y * b.y;
-            acci[q] += vv.x * a.y + vv.y * a.x + ww.x * b.y + ww.y * b.x;
+            if (V) dfc_mac(acc[q], vv, coefd[i * k + r]);
+            if (W) dfc_mac(acc[q], ww, coefd[m * k + i * k + r]);
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         int r = r0 + q;
-        if (r < k) out[(int64_t)r * N + n] = cmake(accr[q], acci[q]);
+        if (r < k) out[(int64_t)r * N + n] = dfc_value(acc[q]);
       }
     }
   }
 }
 
-// y[r] -= sum_i V[i] c[r*ldc + i]
 __global__ void ts_subtract_kernel(const cplx* __restrict__ V, int m,
                                    const cplx* __restrict__ c, int ldc, int k,
                                    int64_t N, cplx* __restrict__ y) {
-  extern __shared__ cplx coef[];  // [k][m]
+  extern __shared__ dfc coefd[];  // [k][m]
   for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
     int r = e / m, i = e % m;
-    coef[e] = c[i * ldc + r];
+    coefd[e] = to_dfc(c[i * ldc + r]);
   }
   __syncthreads();
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
        n += (int64_t)gridDim.x * blockDim.x) {
     for (int r0 = 0; r0 < k; r0 += 8) {
-      double accr[8], acci[8];
+      float acc[8][4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) accr[q] = acci[q] = 0.0;
+      for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
       for (int i = 0; i < m; ++i) {
-        cplx vv = V[(int64_t)i * N + n];
+        const dfc vv = to_dfc(V[(int64_t)i * N + n]);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           int r = r0 + q;
-          if (r < k) {
-            cplx a = coef[r * m + i];
-            accr[q] += vv.x * a.x - vv.y * a.y;
-            acci[q] += vv.x * a.y + vv.y * a.x;
-          }
+          if (r < k) dfc_mac(acc[q], vv, coefd[r * m + i]);
         }
       }
 #pragma unroll
@@ -406,8 +449,8 @@ __global__ void ts_subtract_kernel(const cplx* __restrict__ V, int m,
         int r = r0 + q;
         if (r < k) {
           cplx* d = y + (int64_t)r * N + n;
-          cplx o = *d;
-          *d = cmake(o.x - accr[q], o.y - acci[q]);
+          const cplx o = *d, a = dfc_value(acc[q]);
+          *d = cmake(o.x - a.x, o.y - a.y);
         }
       }
     }
