@@ -65,6 +65,25 @@ def workload_config(prec):
 
 # --------------------------------------------------------------- helpers
 
+def max_over_ranks(ms, ws, device):
+    """The slowest rank's time (ms): every rank contributes its own timed
+    region, the job takes as long as the slowest replica."""
+    if ws <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, units_per_step, steps, t_max_ms):
+    """Units per second over all ranks (weak scaling: each rank does
+    units_per_step per step on its own replica)."""
+    return ws * units_per_step * steps / (t_max_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -256,15 +275,9 @@ def run_ours(args):
     cnt, kms, kfl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
     lib.cvsadc_kernel_stats(kid, ctypes.byref(cnt), ctypes.byref(kms), ctypes.byref(kfl))
     # max time over ranks
-    t_max = ms_total
-    if ws > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms_total, ws, dev)
     ms_per_step = t_max / args.steps
-    value = ws * NVEC * args.steps / (t_max / 1e3)
+    value = whole_job_rate(ws, NVEC, args.steps, t_max)
 
     # roofline of the dominant kernel (CUDA-event timed inside the region)
     peaks = measured_peaks()
@@ -445,6 +458,48 @@ def run_profile_gemm(args):
     print(json.dumps({"profile_gemm": "4096^3", "precision": args.precision}))
 
 
+def run_batched(args):
+    """The batched workload: the first K of the 48 ragged instances (ncore 6,
+    nval U{20..80}, nvirt U{100..400}, naux 5 nvirt, 4 roots, seeds 1000+i),
+    solved through cvsadc_solve_batched with one lane and with four."""
+    import torch
+
+    import paper_2604_27451_gb300 as pkg
+    from synth import batched_shapes
+
+    shapes = batched_shapes(48)[: args.batched]
+    insts = []
+    for sh in shapes:
+        inst = make_instance(sh["ncore"], sh["nval"], sh["nvirt"], sh["naux"], seed=sh["seed"])
+        insts.append(dict(eps=torch.from_numpy(inst.eps).cuda(),
+                          B=torch.from_numpy(inst.B).cuda(), dip=None,
+                          ncore=sh["ncore"], nval=sh["nval"], nvirt=sh["nvirt"]))
+        del inst
+    ctx = pkg.Context(0)
+    out = {"metric": "batched CVS-ADC(2) instances/s", "unit": "instances/s",
+           "config": {"workload": "first %d of 48 ragged instances: ncore 6, nval U{20..80}, "
+                                  "nvirt U{100..400}, naux 5 nvirt, 4 roots, residual 1e-6, "
+                                  "SLICE4 + refinement, inputs resident" % len(shapes),
+                      "shapes": [(s["nval"], s["nvirt"], s["naux"]) for s in shapes]}}
+    omegas = {}
+    for lanes in (1, 4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.solve_batched(insts, 4, precision="slice4", conv=1e-6, lanes=lanes)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        omegas[lanes] = np.array([r["omega"].cpu().numpy() for r in res])
+        out["lanes_%d" % lanes] = {
+            "s": round(dt, 3), "value": round(len(insts) / dt, 4),
+            "status": [r["status"] for r in res],
+            "iterations": [r["info"]["iterations"] for r in res],
+            "t_total_s": [round(r["info"]["t_total_ms"] / 1e3, 2) for r in res]}
+    out["speedup_4_lanes"] = round(out["lanes_1"]["s"] / out["lanes_4"]["s"], 3)
+    out["max_abs_root_diff_lanes"] = float(np.abs(omegas[1] - omegas[4]).max())
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -457,6 +512,8 @@ def main():
                     help="only the timed sigma steps (used for profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--batched", type=int, default=0,
+                    help="time K instances of the batched workload instead")
     ap.add_argument("--ttr-medium-fp64", action="store_true",
                     help="also time the FP64 solve of the medium workload (minutes)")
     ap.add_argument("--profile-gemm", action="store_true",
@@ -464,6 +521,8 @@ def main():
     args = ap.parse_args()
     if args.profile_gemm:
         run_profile_gemm(args)
+    elif args.batched:
+        run_batched(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
