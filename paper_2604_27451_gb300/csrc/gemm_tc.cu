@@ -894,9 +894,19 @@ size_t slice_workspace_bytes(int M, int N, int K, int nslices) {
   return d.a_bytes + d.b_bytes + d.e_bytes + 256;
 }
 
+size_t slice_bcache_bytes(int M, int N, int K, int nslices, int* kc,
+                          size_t* a_bytes) {
+  SDims d = sdims_of(M, N, K, nslices);
+  const int64_t nch = ((int64_t)K + d.kc - 1) / d.kc;
+  if (kc) *kc = d.kc;
+  if (a_bytes) *a_bytes = d.a_bytes;
+  return (size_t)nch * (d.b_bytes + ((size_t)d.Np2 / 2 + 64) * sizeof(int)) + 256;
+}
+
 void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
                  double alpha, View A, View B, double beta, View C, void* work,
-                 size_t work_bytes, cplx* part, size_t part_elems, int* err) {
+                 size_t work_bytes, cplx* part, size_t part_elems, int* err,
+                 SliceBCache* bc) {
   if (M <= 0 || N <= 0) return;
   CVS_REQUIRE(nslices == 4 || nslices == 7, -1, "zgemm_slice: 4 or 7 slices");
   SDims d = sdims_of(M, N, K, nslices);
@@ -912,28 +922,45 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
   int* eA = (int*)((char*)work + d.a_bytes + d.b_bytes);
   int* eB = eA + d.Mp;
   const int64_t tiles = (int64_t)(d.Np2 / SBN) * (d.Mp / BM);
+  const int64_t nch = ((int64_t)K + d.kc - 1) / d.kc;
+  const size_t eb_n = (size_t)d.Np2 / 2 + 64;
+  CVS_REQUIRE(!bc || bc->bytes >= (size_t)nch * (d.b_bytes + eb_n * sizeof(int)),
+              -1, "zgemm_slice: B cache too small");
   for (int k0 = 0; k0 < K; k0 += d.kc) {
     const int Kc = std::min(d.kc, K - k0);
     const int Kp = (Kc + BK - 1) / BK * BK;
+    const int64_t ci = k0 / d.kc;
+    // B's packed slices and exponents: this chunk's slot of the cache, or
+    // the workspace
+    __nv_bfloat16* bpc = bc ? (__nv_bfloat16*)((char*)bc->base + ci * d.b_bytes) : bp;
+    int* eBc = bc ? (int*)((char*)bc->base + nch * d.b_bytes) + ci * eb_n : eB;
+    const bool pack_b = !bc || !bc->filled;
     row_exp_kernel<<<std::min(M, 152 * 16), 256, 0, s>>>(A, M, Kc, k0, eA);
     CVS_CHECK_LAUNCH();
-    col_exp_kernel<<<std::min(N, 152 * 16), 256, 0, s>>>(B, Kc, k0, N, eB);
-    CVS_CHECK_LAUNCH();
+    if (pack_b) {
+      col_exp_kernel<<<std::min(N, 152 * 16), 256, 0, s>>>(B, Kc, k0, N, eBc);
+      CVS_CHECK_LAUNCH();
+    }
     const unsigned ga = grid1d((int64_t)d.Mp * Kp, 256);
     const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * Kp, 256);
     if (nslices == 4) {
       slice_pack_a<4><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, d.npairs, eA, ap);
       CVS_CHECK_LAUNCH();
-      slice_pack_b<4><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eB, bp);
+      if (pack_b) {
+        slice_pack_b<4><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eBc, bpc);
+        CVS_CHECK_LAUNCH();
+      }
     } else {
       slice_pack_a<7><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, d.npairs, eA, ap);
       CVS_CHECK_LAUNCH();
-      slice_pack_b<7><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eB, bp);
+      if (pack_b) {
+        slice_pack_b<7><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eBc, bpc);
+        CVS_CHECK_LAUNCH();
+      }
     }
-    CVS_CHECK_LAUNCH();
     const int64_t kcols = (int64_t)2 * d.npairs * Kp;
     CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
-    CUtensorMap mb = make_map(bp, d.Np2, kcols, SBN);
+    CUtensorMap mb = make_map(bpc, d.Np2, kcols, SBN);
     const int ktpp = 2 * Kp / BK;
     int sp = tc_splits(tiles, ktpp, RUN_KT);
     if (part == nullptr || (size_t)sp * M * N > part_elems) sp = 1;
@@ -943,12 +970,13 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
     dim3 grid(d.Np2 / SBN, d.Mp / BM, nz);
     const int tok = kstats_begin(s, K_TC_SLICE, 8.0 * M * N * (double)Kc);
     tc_slice_kernel<<<grid, 576, S_SMEM, s>>>(ma, mb, d.npairs, ktpp, zl, M, N,
-                                              eA, eB, alpha, beta_c, C,
+                                              eA, eBc, alpha, beta_c, C,
                                               nz > 1 ? part : nullptr, err);
     CVS_CHECK_LAUNCH();
     kstats_end(s, tok);
     if (nz > 1) splitk_reduce(s, M, N, nz, part, beta_c, C);
   }
+  if (bc) bc->filled = true;
 }
 
 }  // namespace cvs

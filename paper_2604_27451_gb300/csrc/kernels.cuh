@@ -31,9 +31,19 @@ bool tc_available();
 // nslices = 4 (10 slice products, ~2^-28 of row max x column max) or 7
 // (28 products, FP64 class).
 size_t slice_workspace_bytes(int M, int N, int K, int nslices);
+// Packed slices (and column exponents) of a B operand that does not change
+// between calls, for every K chunk; filled by the first call that gets it.
+struct SliceBCache {
+  void* base = nullptr;
+  size_t bytes = 0;
+  bool filled = false;
+};
+// bytes such a cache needs for this product (and the K chunk used)
+size_t slice_bcache_bytes(int M, int N, int K, int nslices, int* kc,
+                          size_t* a_bytes);
 void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
                  double alpha, View A, View B, double beta, View C, void* work,
-                 size_t work_bytes, cplx* part, size_t part_elems, int* err);
+                 size_t work_bytes, cplx* part, size_t part_elems, int* err, SliceBCache* bc = nullptr);
 
 // C = beta * C over a view
 void scale_view(cudaStream_t s, int M, int N, double beta, View C, int batch);

@@ -33,6 +33,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <array>
 #include <complex>
 #include <condition_variable>
 #include <new>
@@ -171,6 +172,19 @@ struct cvsadc_ctx {
   double sch_theta = 0.0, sch_ms = 0.0;
   int sch_builds = 0, sch_couplings = 0;
 
+  // packed slices of static B^P operands (key: view geometry, sizes,
+  // slice count, K chunk), valid for the prepared problem
+  struct BEntry {
+    DBuf buf;
+    SliceBCache sc;
+  };
+  std::map<std::array<int64_t, 12>, std::unique_ptr<BEntry>> bcache;
+  size_t bcache_bytes = 0;
+  void clear_bcache() {
+    bcache.clear();
+    bcache_bytes = 0;
+  }
+
   // worker contexts of cvsadc_solve_batched (own streams), kept for reuse
   std::vector<cvsadc_ctx*> lanes;
 
@@ -188,9 +202,10 @@ struct cvsadc_ctx {
     prepared = false;
     for (DBuf* b : problem_buffers()) b->release();
     sch_on = false;
+    clear_bcache();
   }
   size_t held_bytes() {
-    size_t t = s_kpart.bytes + err.bytes;
+    size_t t = s_kpart.bytes + err.bytes + bcache_bytes;
     for (DBuf* b : problem_buffers()) t += b->bytes;
     return t;
   }
@@ -208,6 +223,43 @@ bool needs_refine(int p) {
 }
 
 // --------------------------------------------------------------- GEMM hub
+// A cache slot for the packed slices of B when B is a view of the prepared
+// B^P (it does not change between calls), its packs dwarf those of A (so
+// the K chunking does not depend on the number of trial vectors), and the
+// cache stays within min(25 % of free memory, 48 GB); else NULL.
+constexpr double BCACHE_MAX = 48e9;
+SliceBCache* b_cache(cvsadc_ctx* c, int ns, int M, int N, int K, const View& B) {
+  if (!c->B.p) return nullptr;
+  const cplx* b0 = c->B.c();
+  const size_t nb = c->B.bytes / sizeof(cplx);
+  if (!b0 || B.p < b0 || B.p >= b0 + nb) return nullptr;
+  int kc = 0;
+  size_t a_bytes = 0;
+  const size_t bytes = slice_bcache_bytes(M, N, K, ns, &kc, &a_bytes);
+  if (bytes < 4 * a_bytes) return nullptr;
+  const std::array<int64_t, 12> key = {(int64_t)(B.p - b0), B.rs_hi, B.rs_lo, B.r_lo,
+                                       B.cs_hi, B.cs_lo, B.c_lo, B.conj, N, K, ns, kc};
+  auto it = c->bcache.find(key);
+  if (it != c->bcache.end()) return &it->second->sc;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if ((double)(c->bcache_bytes + bytes) > std::min(0.25 * (double)free_b, BCACHE_MAX))
+    return nullptr;
+  auto e = std::make_unique<cvsadc_ctx::BEntry>();
+  e->buf.ensure(bytes);
+  e->sc.base = e->buf.p;
+  e->sc.bytes = bytes;
+  e->sc.filled = false;
+  c->bcache_bytes += bytes;
+  SliceBCache* r = &e->sc;
+  c->bcache[key] = std::move(e);
+  return r;
+}
+
+
 void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
           View B, double beta, View C, int batch = 1) {
   A = checked(A);
@@ -239,7 +291,7 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
       if (ns)
         zgemm_slice(c->stream, ns, M, N, K, alpha, a, b, beta, cc, c->s_tc.p,
                     need, c->s_kpart.c(), c->s_kpart.bytes / sizeof(cplx),
-                    c->err.as<int>());
+                    c->err.as<int>(), batch == 1 ? b_cache(c, ns, M, N, K, b) : nullptr);
       else
         zgemm_tc(c->stream, 3, M, N, K, alpha, a, b, beta, cc, c->s_tc.p, need,
                  c->s_kpart.c(), c->s_kpart.bytes / sizeof(cplx),
@@ -672,6 +724,7 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   c->prepared = false;
   c->sch_on = false;
   c->sch_g.release();
+  c->clear_bcache();
   c->ncore = p->ncore;
   c->nval = p->nval;
   c->nvirt_in = c->nvirt = p->nvirt;
@@ -689,6 +742,7 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   if (c->has_fns) {
     build_fns(c, prec, p->fns_threshold);
     set_sizes(c);
+    c->clear_bcache();  // B^P was rotated
   }
   auto stage = [&](const char* what, double t) {
     if (verbose()) {
@@ -1827,6 +1881,15 @@ double estimate_bytes(const cvsadc_params* p) {
     b += w;
   }
   b += (double)(8 << 20) * z + 1024;        // split-K scratch, error flag
+  // cached B^P slice packs: the sigma products with N = v L and K = v L
+  // and the preconditioner's (aj|bc) product, 8 npairs v^2 L bytes each
+  {
+    const double pairs = (p->precision == CVSADC_FP64_SLICE7 || needs_refine(p->precision))
+                             ? 10.0 + 28.0 : 10.0;
+    double cb = schur_on ? 8.0 * 10.0 * v * v * L : 0.0;
+    if (p->precision != CVSADC_FP64) cb += 2.0 * 8.0 * pairs * v * v * L;
+    b += std::min(48e9, cb);
+  }
   // Schur-complement preconditioner (when the singles space allows it)
   if (N1 <= 4096 && !(p->flags & CVSADC_FLAG_DIAG_PRECOND)) {
     const double v3 = v * v * v;
