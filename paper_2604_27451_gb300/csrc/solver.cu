@@ -822,10 +822,10 @@ int schur_jchunk(cvsadc_ctx* c) {
   return (int)std::max(1.0, std::min((double)c->nval, 6e9 / per_j));
 }
 
-// S(theta) into sch_S, then its eigen-decomposition into sch_U / sch_lam
+// S(theta) into sch_S (schur_eigh decomposes it)
 void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached) {
   const int nc = c->ncore, nw = c->nval, v = c->nvirt;
-  const int64_t N1 = c->N1, v3 = (int64_t)v * v * v;
+  const int64_t v3 = (int64_t)v * v * v;
   cudaStream_t s = c->stream;
   const int jc = schur_jchunk(c);
   CVS_CUDA(cudaMemsetAsync(c->sch_C11.p, 0, (size_t)nc * v * v * sizeof(cplx), s));
@@ -977,12 +977,10 @@ double small_eigh_lowest(std::vector<std::complex<double>>& A, int p,
   return A[(size_t)best * p + best].real();
 }
 
-// buffers of the preconditioner and the <Kb||Ij> tensor
-void schur_init(cvsadc_ctx* c, int prec) {
-  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
-            L = c->naux;
-  const int64_t N1 = c->N1, nn = (int64_t)n * n;
-  cudaStream_t s = c->stream;
+// buffers of the preconditioner (sized for the prepared problem)
+void schur_init(cvsadc_ctx* c) {
+  const int nc = c->ncore, v = c->nvirt;
+  const int64_t N1 = c->N1;
   const int jc = schur_jchunk(c);
   const int64_t v3 = (int64_t)v * v * v;
   c->sch_S.ensure((size_t)N1 * N1 * sizeof(cplx));
@@ -1007,9 +1005,8 @@ bool schur_setup(cvsadc_ctx* c) {
   c->sch_on = false;
   c->sch_builds = 0;
   c->sch_couplings = 0;
-  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
-            L = c->naux;
-  const int64_t N1 = c->N1, N = c->N, nn = (int64_t)n * n;
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n;
+  const int64_t N1 = c->N1, N = c->N;
   if (N1 > 4096 || v < 2) return false;
   const int prec = schur_precision();
   cudaStream_t s = c->stream;
@@ -1023,7 +1020,7 @@ bool schur_setup(cvsadc_ctx* c) {
   const double emax_c = *std::max_element(eps.begin(), eps.begin() + nc);
   const double emax_w = *std::max_element(eps.begin() + nc, eps.begin() + o);
   const double pole = ev[0] + ev[1] - emax_c - emax_w;
-  schur_init(c, prec);
+  schur_init(c);
   const int jc = schur_jchunk(c);
   const int64_t v3 = (int64_t)v * v * v;
   // keep <ab||cj> when it fits comfortably
@@ -2287,7 +2284,7 @@ int cvsadc_get_schur(cvsadc_ctx* c, double theta, int32_t flags, void* S) {
   return guarded(c, [&] {
     CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
     c->sch_on = false;
-    schur_init(c, CVSADC_FP64);
+    schur_init(c);
     build_schur(c, CVSADC_FP64, theta, false);
     download(c, S, c->sch_S.p, (size_t)c->N1 * c->N1 * sizeof(cplx),
              (flags & CVSADC_FLAG_DEVICE_PTRS) != 0);
