@@ -5,7 +5,7 @@ dimension.  FP64 tolerances follow from the arithmetic: every quantity is
 a sum of O(K) products in FP64 with a different summation order than the
 oracle, so the element-wise error bound is ~K * 2^-53 * sum|a||b|; the
 tests use 1e-11 relative to the largest entry (K <= 10^4 here), and 1e-9
-Eh absolute on eigenvalues (the spec bar for the FP64 path).
+Eh absolute on eigenvalues (the accuracy required of the FP64 path).
 """
 
 import json
