@@ -186,6 +186,8 @@ double fold_norm(cudaStream_t s, const cplx* u, int64_t N, int64_t N1, int nc,
                  double* part);
 void eig_shift(cudaStream_t s, cplx* Y, int64_t n1, int k, const double* lam,
                const double* theta);
+void diag_precond(cudaStream_t s, const cplx* r, double theta,
+                  const double* diag, int64_t N, cplx* out);
 void add_singles(cudaStream_t s, const cplx* a, const cplx* b, int64_t N,
                  int64_t n1, int k, cplx* out);
 

@@ -361,7 +361,9 @@ __global__ void fold_doubles_kernel(const cplx* __restrict__ R,
       const int64_t e = (int64_t)r * N + base + b;
       cplx x = R ? R[e] : cmake(0, 0);
       if (U2) x = cadd(x, U2[e]);
-      outr[base + b] = cscale(x, 1.0 / (th - (e0 + eps[o + b])));
+      double den = th - (e0 + eps[o + b]);
+      if (fabs(den) < 1e-4) den = den < 0 ? -1e-4 : 1e-4;
+      outr[base + b] = cscale(x, 1.0 / den);
     }
   }
 }
@@ -389,6 +391,18 @@ __global__ void fold_norm_kernel(const cplx* __restrict__ u, int64_t N1,
   }
   acc = sum_block(acc);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// out[n] = r[n] / (theta - diag[n]) (the diagonal preconditioner), one vector
+__global__ void diag_precond_kernel(const cplx* __restrict__ r, double theta,
+                                    const double* __restrict__ diag, int64_t N,
+                                    cplx* __restrict__ out) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    double den = theta - diag[n];
+    if (fabs(den) < 1e-4) den = den < 0 ? -1e-4 : 1e-4;
+    out[n] = cscale(r[n], 1.0 / den);
+  }
 }
 
 // Y[i][r] /= (theta_r - lam_i), Y is [n1][k]
@@ -531,6 +545,12 @@ double fold_norm(cudaStream_t s, const cplx* u, int64_t N, int64_t N1, int nc,
   double t = 0.0;
   for (double x : hp) t += x;
   return t;
+}
+
+void diag_precond(cudaStream_t s, const cplx* r, double theta,
+                  const double* diag, int64_t N, cplx* out) {
+  diag_precond_kernel<<<grid1d(N, 256), 256, 0, s>>>(r, theta, diag, N, out);
+  CVS_CHECK_LAUNCH();
 }
 
 void eig_shift(cudaStream_t s, cplx* Y, int64_t n1, int k, const double* lam,

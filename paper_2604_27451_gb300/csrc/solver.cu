@@ -169,7 +169,7 @@ struct cvsadc_ctx {
   DBuf sch_W, sch_g, sch_S, sch_U, sch_V, sch_lam, sch_C11, sch_C12, sch_work,
       sch_tmp, sch_th;
   bool sch_on = false;
-  double sch_theta = 0.0, sch_ms = 0.0;
+  double sch_theta = 0.0, sch_ms = 0.0, sch_pole = 0.0;
   int sch_builds = 0, sch_couplings = 0;
 
   // packed slices of static B^P operands (key: view geometry, sizes,
@@ -1020,6 +1020,7 @@ bool schur_setup(cvsadc_ctx* c) {
   const double emax_c = *std::max_element(eps.begin(), eps.begin() + nc);
   const double emax_w = *std::max_element(eps.begin() + nc, eps.begin() + o);
   const double pole = ev[0] + ev[1] - emax_c - emax_w;
+  c->sch_pole = pole;
   schur_init(c);
   const int jc = schur_jchunk(c);
   const int64_t v3 = (int64_t)v * v * v;
@@ -1192,9 +1193,10 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     CVS_CUDA(cudaMemcpyAsync(V, X0, (size_t)nx0 * N * sizeof(cplx),
                              cudaMemcpyDeviceToDevice, s));
     nguess = nx0;
-  } else if (schur) {
+  } else if (schur && std::min<int64_t>(std::min(nguess, 64), c->N1) >= k) {
     // the lowest eigenvectors u of S(theta0) with their folded doubles
-    // (theta0 - M22)^-1 M21 u, built in W then compacted into V below
+    // (theta0 - M22)^-1 M21 u, built in W then compacted into V below (used
+    // when they can cover every wanted root)
     nguess = (int)std::min<int64_t>(std::min(nguess, 64), c->N1);
     const int64_t N1 = c->N1;
     CVS_CUDA(cudaMemsetAsync(W, 0, (size_t)nguess * N * sizeof(cplx), s));
@@ -1398,6 +1400,12 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
       fold_doubles(s, Tn, Yb, thd, cnt, N, N1, c->ncore, c->nval, c->nvirt,
                    c->eps.d(), false, Z);
       c->sch_couplings += 2 * cnt;
+      // roots at or above the lowest M22 entry: S(theta0) says nothing about
+      // them, so they take the diagonal preconditioner
+      for (int q = 0; q < cnt; ++q)
+        if (tht[q] >= c->sch_pole - 1e-3)
+          diag_precond(s, Tn + (int64_t)q * N, tht[q], c->diag.d(), N,
+                       Z + (int64_t)q * N);
       Tn = Z;
     }
     int added = orthonormalise_append(Tn, (int)todo.size());

@@ -391,3 +391,39 @@ def test_reference_gradient_matches_finite_differences(shape, nroots):
         assert abs(fd - np.sum(ge * de)) < 1e-7 * max(1.0, abs(fd))
     # the projected gradient is Hermitian
     assert np.abs(gB - np.conj(gB.transpose(0, 2, 1))).max() < 1e-14
+
+
+# ------------------------------------- folded doubles (Schur complement)
+
+def test_self_energy_splits_into_five_structured_terms():
+    """M12 (theta - M22)^-1 M21 from the oracle's explicit blocks equals the
+    five pieces the GPU preconditioner builds: a weighted Gram of <ab||cj>
+    per core index, a <ab||cj>-<Kb||Ij> cross term and its adjoint, and two
+    <Kb||Ij> terms (sums over all a, b with w = 1/(theta - M22))."""
+    from oracle.integrals import antisym
+
+    nc, nw, nv, L = 3, 4, 7, 20
+    inst = make_instance(nc, nw, nv, L, seed=1)
+    eps, B = inst.eps, inst.B
+    o = nc + nw
+    C, W, V = np.arange(nc), np.arange(nc, o), np.arange(o, o + nv)
+    M21 = adc2.m21(eps, B, nc, nw, nv)
+    D = adc2.m22(eps, nc, nw, nv).reshape(-1)
+    th = D.min() - 3.0
+    explicit = (M21.conj().T / (th - D)) @ M21
+    g = antisym(B, V, V, V, W)  # <ab||cj>
+    h = antisym(B, C, V, C, W)  # <Kb||Ij>
+    ec, ew, ev = eps[C], eps[W], eps[V]
+    w = 1.0 / (th - (ev[None, None, :, None] + ev[None, None, None, :]
+                     - ec[:, None, None, None] - ew[None, :, None, None]))
+    S = np.zeros((nc, nv, nc, nv), complex)
+    for K in range(nc):
+        S[K, :, K, :] += 0.5 * np.einsum("jab,abcj,abdj->cd", w[K], g.conj(), g)
+    X = -np.einsum("Kjdb,dbcj,EbKj->KcEd", w, g.conj(), h)
+    S += X + np.conj(np.transpose(X, (2, 3, 0, 1)))
+    S22 = np.einsum("Ijcb,KbIj,EbIj->KcE", w, h.conj(), h)
+    for c in range(nv):
+        S[:, c, :, c] += S22[:, c, :]
+    S -= np.einsum("Ijcd,KdIj,EcIj->KcEd", w, h.conj(), h)
+    S = S.reshape(nc * nv, nc * nv)
+    assert np.abs(S - explicit).max() < 1e-13 * np.abs(explicit).max()
