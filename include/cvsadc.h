@@ -153,7 +153,13 @@ const char* cvsadc_last_error(cvsadc_ctx* ctx);
  * the Cholesky vectors, optional frozen-natural-spinor truncation (Eqs.
  * 15, 17-20) with rotation of B^P, the CVS-ADC(2) matrix (Eqs. 11-12 under
  * the CVS restriction), a Davidson eigensolver, and transition moments
- * through first order with oscillator strengths.
+ * through first order with oscillator strengths.  The Davidson solver is
+ * preconditioned with the Schur complement S(theta0) of the diagonal M22
+ * block (see cvsadc_get_schur; info->schur_theta reports theta0) when the
+ * singles space has at most 4096 elements and the lowest root lies below
+ * every M22 entry; CVSADC_FLAG_DIAG_PRECOND selects the diagonal
+ * preconditioner instead.  The preconditioner changes the iteration, not
+ * the converged roots.
  *   omega : [nroots] out, ascending excitation energies (Eh)
  *   X     : [nroots][N] complex out (CVS packed, in the final basis) or NULL;
  *           written only with CVSADC_FLAG_RETURN_X.  The largest-modulus
