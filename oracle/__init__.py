@@ -13,7 +13,11 @@ Modules:
 * ``adc2``      -- CVS spaces and packing, explicit CVS-ADC(2) blocks,
                    matrix-free sigma, transition moments, eigen-solvers;
 * ``fci``       -- determinant-space engine and brute-force ISR, the
-                   independent pin of the ``adc2`` element formulas.
+                   independent pin of the ``adc2`` element formulas;
+* ``grad``      -- the gradient of a sum of roots with respect to the spinor
+                   energies and the Cholesky vectors, by torch autograd of
+                   the explicit matrix (CPU, complex128), pinned by central
+                   differences of ``adc2`` eigenvalues.
 
 Parity status of each function is stated in its docstring.  One gap is
 declared here: the second-order singles part of the modified transition
