@@ -65,11 +65,14 @@ extern "C" {
 
 /* ----------------------------------------------------------- precision */
 #define CVSADC_FP64 0          /* complex128 throughout, FP64 FMA GEMMs */
-#define CVSADC_MIXED_BF16X3 1  /* GEMMs on tcgen05 tensor cores: each real
-                                  value split into bf16 hi + lo, three
-                                  products kept, FP32 accumulation in
-                                  tensor memory; the accumulation limits the
-                                  error to ~1e-5 relative at K ~ 10^3-10^4 */
+#define CVSADC_MIXED_BF16X3 1  /* Davidson sigma GEMMs on tcgen05 tensor
+                                  cores: each real value split into bf16
+                                  hi + lo, three products kept, FP32
+                                  accumulation in tensor memory; the
+                                  accumulation limits the error to ~1e-5
+                                  relative at K ~ 10^3-10^4, so the problem
+                                  itself (t2, M11, couplings, moments) is
+                                  built with the FP64-class 7-slice product */
 #define CVSADC_MIXED_SLICE4 2  /* tensor-core GEMMs on exact integer slices:
                                   per-row/column power-of-two scales, four
                                   7-bit slices per value (10 slice products),
@@ -339,14 +342,28 @@ void cvsadc_kernel_stats_reset(void);
  * overlap on the GPU (other streams or host threads) race on it: serialise
  * them.  Each call writes every partial it reads, so nothing carries over.
  * Errors: CVSADC_EINVAL for NULL pointers, non-positive sizes, a product
- * beyond the limits above, or leading dimensions smaller than the rows;
- * CVSADC_ECUDA for a CUDA error. */
+ * beyond the limits above, or a leading dimension smaller than its row
+ * length (lda < K, ldb < N or ldc < N); CVSADC_ECUDA for a CUDA error. */
 #define CVSADC_NOALLOC_MAX_MN 4096
 #define CVSADC_NOALLOC_MAX_M_PLUS_N 384
 int cvsadc_zgemm_small_noalloc(void* cuda_stream, int32_t M, int32_t N,
                                int32_t K, const void* A, int64_t lda,
                                const void* B, int64_t ldb, void* C,
                                int64_t ldc);
+
+/* Block inner products out[i][j] = sum_n conj(A[i][n]) B[j][n] (i < ma,
+ * j < mb; out host [ma][mb] complex128) of device vectors A [ma][N] and
+ * B [mb][N] (complex128, on the context's device), in the arithmetic the
+ * Davidson solver uses for `precision`: plain FP64 for CVSADC_FP64 and
+ * CVSADC_FP64_SLICE7 (Gram matrices, Gram-Schmidt, Ritz combinations);
+ * double-float on the FP32 pipes for the mixed precisions (float hi/lo
+ * pairs, ~48-bit significand and the float exponent range, tiles of 16
+ * terms summed in FP64).  The section "Implementation and Computational
+ * Details" names Davidson; this exposes its inner product so that callers
+ * can check the arithmetic.  Errors: CVSADC_EINVAL for NULL pointers or
+ * non-positive sizes; CVSADC_ECUDA. */
+int cvsadc_block_dot(cvsadc_ctx* ctx, int32_t precision, const void* A,
+                     int32_t ma, const void* B, int32_t mb, int64_t N, void* out);
 
 /* Davidson on the prepared problem (see cvsadc_solve for outputs). */
 int cvsadc_davidson(cvsadc_ctx* ctx, const cvsadc_params* params,

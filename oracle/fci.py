@@ -291,6 +291,32 @@ class ISR:
         cE = fit([np.array([e]) for e in Es])[:, 0]
         return cM, cF, cE
 
+    def ground_rdm1_taylor(self, order: int = 2, h: float = 0.02, deg: int = 8,
+                           npts: int = 17):
+        """Taylor coefficients [0..order] at lambda = 0 of the exact ground
+        state's one-particle density matrix, gamma[p, q](lambda) =
+        <Psi_0(lambda)| a_p^+ a_q |Psi_0(lambda)>, over all spinors, from the
+        same Chebyshev least-squares fit as ``taylor``.  At lambda^2 its
+        virtual-virtual block is the second-order (MP2) density that Eq. 15
+        writes in closed form."""
+        sp = self.space
+        n = sp.n
+        ops = {(p, q): sp.operator([(1, p), (0, q)]) for p in range(n) for q in range(n)}
+        k = np.arange(npts)
+        lams = h * np.cos((2 * k + 1) * np.pi / (2 * npts))
+        gs = []
+        for lam in lams:
+            Hl = np.diag(self.h0) + lam * self.V
+            _, U = np.linalg.eigh(Hl)
+            psi0 = U[:, 0]
+            g = np.zeros((n, n), dtype=np.complex128)
+            for (p, q), op in ops.items():
+                g[p, q] = np.vdot(psi0, sp.act(op, psi0))
+            gs.append(g)
+        Vm = np.vander(lams / h, deg + 1, increasing=True)
+        c = (np.linalg.pinv(Vm) @ np.stack(gs).reshape(npts, -1)) * (h ** -np.arange(deg + 1))[:, None]
+        return c[: order + 1].reshape(order + 1, n, n)
+
     def rspt_e2(self) -> float:
         """Second-order Rayleigh-Schrodinger energy from the determinant
         space: sum_D |<D|V|Phi0>|^2 / (E0(0) - E_D(0))."""

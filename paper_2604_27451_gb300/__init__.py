@@ -205,6 +205,21 @@ class Context:
                                           pc, N))
         return C
 
+    def block_dot(self, A, B, precision="fp64"):
+        """A^H B (numpy [ma][mb]) of torch CUDA blocks A [ma][N], B [mb][N]
+        in the Davidson solver's arithmetic for `precision`."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        _inputs_ready(A, B)
+        pa, dev = _ptr(A)
+        pb, _ = _ptr(B)
+        if not dev:
+            raise ValueError("block_dot takes device tensors")
+        out = np.empty((A.shape[0], B.shape[0]), dtype=np.complex128)
+        self._check(self.lib.cvsadc_block_dot(self.h, prec, pa, A.shape[0], pb,
+                                              B.shape[0], A.shape[1],
+                                              ctypes.c_void_p(out.ctypes.data)))
+        return out
+
     def davidson(self, nroots, precision="fp64", conv=1e-6, max_iter=0,
                  max_subspace=0, return_x=False, refine=True, precond="schur"):
         s = self._shape

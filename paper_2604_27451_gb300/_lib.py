@@ -94,6 +94,8 @@ _SIGNATURES = {
                                                   ctypes.c_int32, _vp, ctypes.c_int64,
                                                   _vp, ctypes.c_int64, _vp,
                                                   ctypes.c_int64]),
+    "cvsadc_block_dot": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp,
+                                        ctypes.c_int32, ctypes.c_int64, _vp]),
     "cvsadc_launch_count": (ctypes.c_int64, []),
     "cvsadc_kernel_timing": (None, [ctypes.c_int32]),
     "cvsadc_kernel_stats": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),

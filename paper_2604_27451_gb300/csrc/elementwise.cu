@@ -111,6 +111,84 @@ __global__ void t2_band_kernel(const cplx* __restrict__ V, int a0, int na,
   if (threadIdx.x == 0) part[blockIdx.x] += s;
 }
 
+// In-place band transform.  X holds a band [al][i][b][j] = (a i | b j)
+// (a = a0 + al, i, j occupied, b virtual).  Each CTA takes one (al, b) and
+// one pair of 32 x 32 tiles (i-tile ti <= j-tile tj) together with its
+// mirror, stages both in shared memory (coalesced rows) and writes
+//   X[al][i][b][j] <- <ab||ij> = (a i|b j) - (a j|b i)
+//   T[al][i][b][j]  = <ab||ij> / (e_i + e_j - e_a - e_b)
+// for both tiles, so each (i, j), (j, i) pair is read and written by one
+// CTA only.  part[block] = the block's share of E_MP2 = 1/4 sum |g|^2 / den.
+constexpr int TB2 = 32;
+__global__ void t2_band_ip_kernel(cplx* __restrict__ X, cplx* __restrict__ T,
+                                  int a0, int o, int v,
+                                  const double* __restrict__ eps, int ntile,
+                                  double* __restrict__ part) {
+  __shared__ cplx sa[TB2][TB2 + 1], sb[TB2][TB2 + 1];
+  const int npt = ntile * (ntile + 1) / 2;
+  const int64_t blk = blockIdx.x;
+  const int tp = (int)(blk % npt);
+  const int64_t ab = blk / npt;
+  const int b = (int)(ab % v);
+  const int al = (int)(ab / v);
+  int ti = 0, rem = tp;
+  while (rem >= ntile - ti) {
+    rem -= ntile - ti;
+    ++ti;
+  }
+  const int tj = ti + rem;
+  const int i0 = ti * TB2, j0 = tj * TB2;
+  const bool dg = ti == tj;
+  const int64_t vo = (int64_t)v * o;
+  cplx* Xa = X + (int64_t)al * o * vo + (int64_t)b * o;  // (i, j) -> i vo + j
+  cplx* Ta = T + (int64_t)al * o * vo + (int64_t)b * o;
+  for (int e = threadIdx.x; e < TB2 * TB2; e += blockDim.x) {
+    const int r = e / TB2, cc = e % TB2;
+    const int i = i0 + r, j = j0 + cc;
+    sa[r][cc] = (i < o && j < o) ? Xa[(int64_t)i * vo + j] : cmake(0, 0);
+    if (!dg) {
+      const int jj = j0 + r, ii = i0 + cc;
+      sb[r][cc] = (jj < o && ii < o) ? Xa[(int64_t)jj * vo + ii] : cmake(0, 0);
+    }
+  }
+  __syncthreads();
+  const double eab = eps[o + a0 + al] + eps[o + b];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < TB2 * TB2; e += blockDim.x) {
+    const int r = e / TB2, cc = e % TB2;
+    {
+      const int i = i0 + r, j = j0 + cc;
+      if (i < o && j < o) {
+        const cplx xji = dg ? sa[cc][r] : sb[cc][r];
+        const cplx g = csub(sa[r][cc], xji);
+        const double den = eps[i] + eps[j] - eab;
+        Xa[(int64_t)i * vo + j] = g;
+        Ta[(int64_t)i * vo + j] = cscale(g, 1.0 / den);
+        acc += (dg ? 0.25 : 0.5) * (g.x * g.x + g.y * g.y) / den;
+      }
+    }
+    if (!dg) {
+      const int jj = j0 + r, ii = i0 + cc;
+      if (jj < o && ii < o) {
+        const cplx g = csub(sb[r][cc], sa[cc][r]);
+        const double den = eps[ii] + eps[jj] - eab;
+        Xa[(int64_t)jj * vo + ii] = g;
+        Ta[(int64_t)jj * vo + ii] = cscale(g, 1.0 / den);
+      }
+    }
+  }
+  const double sum = block_sum(acc);
+  if (threadIdx.x == 0) part[blk] = sum;
+}
+
+// *out += sum of in[0..n)
+__global__ void reduce_sum_add_kernel(const double* in, int64_t n, double* out) {
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += in[i];
+  double s = block_sum(acc);
+  if (threadIdx.x == 0) *out += s;
+}
+
 __global__ void reduce_sum_kernel(const double* in, int n, double* out) {
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += in[i];
@@ -321,14 +399,52 @@ __device__ __forceinline__ cplx dfc_value(const float* acc) {
   return cmake((double)acc[0] + (double)acc[1], (double)acc[2] + (double)acc[3]);
 }
 
+// Arithmetic policies of the tall-skinny kernels: ArDF is the double-float
+// arithmetic above (mixed precisions), Ar64 plain FP64 (FP64-class
+// precisions).  E is the element type staged in shared memory, Acc an
+// accumulator of one complex sum.
+struct ArDF {
+  typedef dfc E;
+  struct Acc {
+    float v[4];
+  };
+  __device__ static E load(cplx x) { return to_dfc(x); }
+  __device__ static void zero(Acc& a) { a.v[0] = a.v[1] = a.v[2] = a.v[3] = 0.f; }
+  __device__ static void cmac(Acc& a, const E& x, const E& y) { dfc_conj_mac(a.v, x, y); }
+  __device__ static void mac(Acc& a, const E& x, const E& y) { dfc_mac(a.v, x, y); }
+  __device__ static cplx value(const Acc& a) { return dfc_value(a.v); }
+};
+struct Ar64 {
+  typedef cplx E;
+  struct Acc {
+    double re, im;
+  };
+  __device__ static E load(cplx x) { return x; }
+  __device__ static void zero(Acc& a) { a.re = a.im = 0.0; }
+  __device__ static void cmac(Acc& a, const E& x, const E& y) {
+    a.re = fma(x.x, y.x, fma(x.y, y.y, a.re));
+    a.im = fma(x.x, y.y, fma(-x.y, y.x, a.im));
+  }
+  __device__ static void mac(Acc& a, const E& x, const E& y) {
+    a.re = fma(x.x, y.x, fma(-x.y, y.y, a.re));
+    a.im = fma(x.x, y.y, fma(x.y, y.x, a.im));
+  }
+  __device__ static cplx value(const Acc& a) { return cmake(a.re, a.im); }
+};
+static_assert(sizeof(ArDF::E) == sizeof(cplx) && sizeof(Ar64::E) == sizeof(cplx),
+              "staged elements are 16 bytes under both policies");
+
 constexpr int TSN = 16;  // n-tile of ts_dot
 
+template <class P>
 __global__ void ts_dot_kernel(const cplx* __restrict__ A, int ma,
                               const cplx* __restrict__ B, int mb, int64_t N,
                               cplx* __restrict__ part) {
-  extern __shared__ dfc shd[];
-  dfc* sa = shd;             // [ma][TSN]
-  dfc* sb = shd + ma * TSN;  // [mb][TSN]
+  extern __shared__ __align__(16) unsigned char ts_sm[];
+  typedef typename P::E E;
+  E* shd = (E*)ts_sm;
+  E* sa = shd;             // [ma][TSN]
+  E* sb = shd + ma * TSN;  // [mb][TSN]
   const int npairs = ma * mb;
   const int per = (npairs + blockDim.x - 1) / blockDim.x;  // <= 16
   double ar[16], ai[16];
@@ -342,19 +458,20 @@ __global__ void ts_dot_kernel(const cplx* __restrict__ A, int ma,
       int64_t n = t0 + k;
       cplx val = cmake(0, 0);
       if (n < n1) val = vec < ma ? A[(int64_t)vec * N + n] : B[(int64_t)(vec - ma) * N + n];
-      shd[e] = to_dfc(val);
+      shd[e] = P::load(val);
     }
     __syncthreads();
     for (int q = 0; q < per; ++q) {
       int pr = threadIdx.x + q * blockDim.x;
       if (pr >= npairs) break;
       int i = pr / mb, j = pr % mb;
-      const dfc* x = sa + i * TSN;
-      const dfc* y = sb + j * TSN;
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const E* x = sa + i * TSN;
+      const E* y = sb + j * TSN;
+      typename P::Acc acc;
+      P::zero(acc);
 #pragma unroll
-      for (int k = 0; k < TSN; ++k) dfc_conj_mac(acc, x[k], y[k]);
-      const cplx v = dfc_value(acc);
+      for (int k = 0; k < TSN; ++k) P::cmac(acc, x[k], y[k]);
+      const cplx v = P::value(acc);
       ar[q] += v.x;
       ai[q] += v.y;
     }
@@ -382,66 +499,72 @@ __global__ void ts_dot_reduce(const cplx* part, int npairs, int mb,
 }
 
 // out[r][n] = sum_i W[i][n] cw[i*ldc+r] + V[i][n] cv[i*ldc+r]
+template <class P>
 __global__ void ts_combine_kernel(const cplx* __restrict__ V,
                                   const cplx* __restrict__ cv,
                                   const cplx* __restrict__ W,
                                   const cplx* __restrict__ cw, int m, int ldc,
                                   int k, int64_t N, cplx* __restrict__ out) {
-  extern __shared__ dfc coefd[];  // [2][m][k]
+  extern __shared__ __align__(16) unsigned char ts_sm[];
+  typedef typename P::E E;
+  E* coefd = (E*)ts_sm;  // [2][m][k]
   for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
     int i = e / k, r = e % k;
-    coefd[e] = to_dfc(cv ? cv[i * ldc + r] : cmake(0, 0));
-    coefd[m * k + e] = to_dfc(cw ? cw[i * ldc + r] : cmake(0, 0));
+    coefd[e] = P::load(cv ? cv[i * ldc + r] : cmake(0, 0));
+    coefd[m * k + e] = P::load(cw ? cw[i * ldc + r] : cmake(0, 0));
   }
   __syncthreads();
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
        n += (int64_t)gridDim.x * blockDim.x) {
     for (int r0 = 0; r0 < k; r0 += 8) {
-      float acc[8][4];
+      typename P::Acc acc[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+      for (int q = 0; q < 8; ++q) P::zero(acc[q]);
       for (int i = 0; i < m; ++i) {
-        const dfc vv = to_dfc(V ? V[(int64_t)i * N + n] : cmake(0, 0));
-        const dfc ww = to_dfc(W ? W[(int64_t)i * N + n] : cmake(0, 0));
+        const E vv = P::load(V ? V[(int64_t)i * N + n] : cmake(0, 0));
+        const E ww = P::load(W ? W[(int64_t)i * N + n] : cmake(0, 0));
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           int r = r0 + q;
           if (r < k) {
-            if (V) dfc_mac(acc[q], vv, coefd[i * k + r]);
-            if (W) dfc_mac(acc[q], ww, coefd[m * k + i * k + r]);
+            if (V) P::mac(acc[q], vv, coefd[i * k + r]);
+            if (W) P::mac(acc[q], ww, coefd[m * k + i * k + r]);
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         int r = r0 + q;
-        if (r < k) out[(int64_t)r * N + n] = dfc_value(acc[q]);
+        if (r < k) out[(int64_t)r * N + n] = P::value(acc[q]);
       }
     }
   }
 }
 
+template <class P>
 __global__ void ts_subtract_kernel(const cplx* __restrict__ V, int m,
                                    const cplx* __restrict__ c, int ldc, int k,
                                    int64_t N, cplx* __restrict__ y) {
-  extern __shared__ dfc coefd[];  // [k][m]
+  extern __shared__ __align__(16) unsigned char ts_sm[];
+  typedef typename P::E E;
+  E* coefd = (E*)ts_sm;  // [k][m]
   for (int e = threadIdx.x; e < m * k; e += blockDim.x) {
     int r = e / m, i = e % m;
-    coefd[e] = to_dfc(c[i * ldc + r]);
+    coefd[e] = P::load(c[i * ldc + r]);
   }
   __syncthreads();
   for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
        n += (int64_t)gridDim.x * blockDim.x) {
     for (int r0 = 0; r0 < k; r0 += 8) {
-      float acc[8][4];
+      typename P::Acc acc[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+      for (int q = 0; q < 8; ++q) P::zero(acc[q]);
       for (int i = 0; i < m; ++i) {
-        const dfc vv = to_dfc(V[(int64_t)i * N + n]);
+        const E vv = P::load(V[(int64_t)i * N + n]);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           int r = r0 + q;
-          if (r < k) dfc_mac(acc[q], vv, coefd[r * m + i]);
+          if (r < k) P::mac(acc[q], vv, coefd[r * m + i]);
         }
       }
 #pragma unroll
@@ -449,7 +572,7 @@ __global__ void ts_subtract_kernel(const cplx* __restrict__ V, int m,
         int r = r0 + q;
         if (r < k) {
           cplx* d = y + (int64_t)r * N + n;
-          const cplx o = *d, a = dfc_value(acc[q]);
+          const cplx o = *d, a = P::value(acc[q]);
           *d = cmake(o.x - a.x, o.y - a.y);
         }
       }
@@ -745,6 +868,22 @@ void t2_band(cudaStream_t s, const cplx* V, int a0, int na, int o, int v,
   CVS_CHECK_LAUNCH();
 }
 
+int64_t t2_band_ip_blocks(int nb, int o, int v) {
+  const int nt = (o + TB2 - 1) / TB2;
+  return (int64_t)nt * (nt + 1) / 2 * nb * v;
+}
+
+void t2_band_inplace(cudaStream_t s, cplx* X, cplx* T, int a0, int nb, int o,
+                     int v, const double* eps, double* part, double* emp2) {
+  const int nt = (o + TB2 - 1) / TB2;
+  const int64_t nblk = t2_band_ip_blocks(nb, o, v);
+  CVS_REQUIRE(nblk < (1LL << 31), -1, "t2_band_inplace: band too large");
+  t2_band_ip_kernel<<<(unsigned)nblk, 256, 0, s>>>(X, T, a0, o, v, eps, nt, part);
+  CVS_CHECK_LAUNCH();
+  reduce_sum_add_kernel<<<1, 256, 0, s>>>(part, nblk, emp2);
+  CVS_CHECK_LAUNCH();
+}
+
 void reduce_sum(cudaStream_t s, const double* in, int n, double* out) {
   reduce_sum_kernel<<<1, 256, 0, s>>>(in, n, out);
   CVS_CHECK_LAUNCH();
@@ -818,23 +957,26 @@ void build_diag(cudaStream_t s, const cplx* M11, const double* eps,
 }
 
 void ts_dot(cudaStream_t s, const cplx* A, int ma, const cplx* B, int mb,
-            int64_t N, cplx* part, cplx* out, int ldo) {
+            int64_t N, cplx* part, cplx* out, int ldo, bool fp64) {
   if (ma > 96) {
     for (int i0 = 0; i0 < ma; i0 += 96)
       ts_dot(s, A + (int64_t)i0 * N, std::min(96, ma - i0), B, mb, N, part,
-             out + (int64_t)i0 * ldo, ldo);
+             out + (int64_t)i0 * ldo, ldo, fp64);
     return;
   }
   if (ma * mb > 16 * 256 || ma + mb > 192) {
     int g = std::max(1, std::min(192 - ma, 4096 / ma));
     for (int j0 = 0; j0 < mb; j0 += g)
       ts_dot(s, A, ma, B + (int64_t)j0 * N, std::min(g, mb - j0), N, part,
-             out + j0, ldo);
+             out + j0, ldo, fp64);
     return;
   }
   int chunks = TS_CHUNKS;
   size_t sh = (size_t)(ma + mb) * TSN * sizeof(cplx);
-  ts_dot_kernel<<<chunks, 256, sh, s>>>(A, ma, B, mb, N, part);
+  if (fp64)
+    ts_dot_kernel<Ar64><<<chunks, 256, sh, s>>>(A, ma, B, mb, N, part);
+  else
+    ts_dot_kernel<ArDF><<<chunks, 256, sh, s>>>(A, ma, B, mb, N, part);
   CVS_CHECK_LAUNCH();
   ts_dot_reduce<<<ma * mb, 256, 0, s>>>(part, ma * mb, mb, chunks, out, ldo);
   CVS_CHECK_LAUNCH();
@@ -842,32 +984,39 @@ void ts_dot(cudaStream_t s, const cplx* A, int ma, const cplx* B, int mb,
 
 void ts_combine(cudaStream_t s, const cplx* V, const cplx* cv, const cplx* W,
                 const cplx* cw, int m, int ldc, int k, int64_t N,
-                cplx* out) {
+                cplx* out, bool fp64) {
   if (2 * (size_t)m * k * sizeof(cplx) > 96 * 1024) {
     int g = std::max(1, (int)(96 * 1024 / (2 * (size_t)m * sizeof(cplx))));
     CVS_REQUIRE(2 * (size_t)m * sizeof(cplx) <= 96 * 1024, -1, "ts_combine: m too large");
     for (int r0 = 0; r0 < k; r0 += g)
       ts_combine(s, V, cv ? cv + r0 : nullptr, W, cw ? cw + r0 : nullptr, m,
-                 ldc, std::min(g, k - r0), N, out + (int64_t)r0 * N);
+                 ldc, std::min(g, k - r0), N, out + (int64_t)r0 * N, fp64);
     return;
   }
   size_t sh = 2 * (size_t)m * k * sizeof(cplx);
-  ts_combine_kernel<<<grid1d(N, 256), 256, sh, s>>>(V, cv, W, cw, m, ldc, k,
-                                                    N, out);
+  if (fp64)
+    ts_combine_kernel<Ar64><<<grid1d(N, 256), 256, sh, s>>>(V, cv, W, cw, m, ldc, k,
+                                                            N, out);
+  else
+    ts_combine_kernel<ArDF><<<grid1d(N, 256), 256, sh, s>>>(V, cv, W, cw, m, ldc, k,
+                                                            N, out);
   CVS_CHECK_LAUNCH();
 }
 
 void ts_subtract(cudaStream_t s, const cplx* V, int m, const cplx* c, int ldc,
-                 int k, int64_t N, cplx* y) {
+                 int k, int64_t N, cplx* y, bool fp64) {
   if ((size_t)m * k * sizeof(cplx) > 96 * 1024) {
     int g = std::max(1, (int)(96 * 1024 / ((size_t)m * sizeof(cplx))));
     for (int r0 = 0; r0 < k; r0 += g)
       ts_subtract(s, V, m, c + r0, ldc, std::min(g, k - r0), N,
-                  y + (int64_t)r0 * N);
+                  y + (int64_t)r0 * N, fp64);
     return;
   }
   size_t sh = (size_t)m * k * sizeof(cplx);
-  ts_subtract_kernel<<<grid1d(N, 256), 256, sh, s>>>(V, m, c, ldc, k, N, y);
+  if (fp64)
+    ts_subtract_kernel<Ar64><<<grid1d(N, 256), 256, sh, s>>>(V, m, c, ldc, k, N, y);
+  else
+    ts_subtract_kernel<ArDF><<<grid1d(N, 256), 256, sh, s>>>(V, m, c, ldc, k, N, y);
   CVS_CHECK_LAUNCH();
 }
 
@@ -926,13 +1075,22 @@ void phase_fix(cudaStream_t s, cplx* x, int k, int64_t N, double* work) {
 }
 
 void init_kernel_attributes() {
-  CVS_CUDA(cudaFuncSetAttribute(ts_combine_kernel,
+  CVS_CUDA(cudaFuncSetAttribute(ts_combine_kernel<ArDF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 96 * 1024));
-  CVS_CUDA(cudaFuncSetAttribute(ts_subtract_kernel,
+  CVS_CUDA(cudaFuncSetAttribute(ts_subtract_kernel<ArDF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 96 * 1024));
-  CVS_CUDA(cudaFuncSetAttribute(ts_dot_kernel,
+  CVS_CUDA(cudaFuncSetAttribute(ts_dot_kernel<ArDF>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024));
+  CVS_CUDA(cudaFuncSetAttribute(ts_combine_kernel<Ar64>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024));
+  CVS_CUDA(cudaFuncSetAttribute(ts_subtract_kernel<Ar64>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                96 * 1024));
+  CVS_CUDA(cudaFuncSetAttribute(ts_dot_kernel<Ar64>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 96 * 1024));
 }

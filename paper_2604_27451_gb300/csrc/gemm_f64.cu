@@ -283,8 +283,12 @@ void zgemm_f64(cudaStream_t s, int M, int N, int K, double alpha, View A,
     return;
   }
   if (batch == 1 && part && smallmn_ok(M, N, K)) {
-    const int nb = smallmn_blocks(M, N, K);
-    if ((size_t)nb * M * N <= part_elems) {
+    // as many K slices as the partial-product scratch holds (a caller with
+    // a small fixed scratch gets fewer, longer slices, never the one-CTA
+    // tile path)
+    const int nb = (int)std::min<int64_t>(smallmn_blocks(M, N, K),
+                                          (int64_t)(part_elems / ((size_t)M * N)));
+    if (nb >= 1) {
       const int kchunk = (K + nb - 1) / nb;
       size_t sh = (size_t)(M + N) * STK * sizeof(cplx);
       zgemm_smallmn_kernel<<<nb, 256, sh, s>>>(M, N, K, alpha, A, B, kchunk,

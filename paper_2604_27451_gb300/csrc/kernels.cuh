@@ -61,6 +61,13 @@ void hermiticity(cudaStream_t s, const cplx* B, int n, int64_t nmat,
 // 1/4 |g2|^2 / den into per-block partials part[nblk].
 void t2_band(cudaStream_t s, const cplx* V, int a0, int na, int o, int v,
              const double* eps, cplx* t2, cplx* g2, double* part, int nblk);
+// Band transform in place: X [al][i][b][j] = (a i|b j) for a = a0 + al
+// becomes <ab||ij>, T (same layout) = t^{ab}_{ij}; *emp2 (device) += the
+// band's share of E_MP2.  part must hold t2_band_ip_blocks(nb, o, v)
+// doubles.
+int64_t t2_band_ip_blocks(int nb, int o, int v);
+void t2_band_inplace(cudaStream_t s, cplx* X, cplx* T, int a0, int nb, int o,
+                     int v, const double* eps, double* part, double* emp2);
 // Deterministic sum of n doubles into *out (device).
 void reduce_sum(cudaStream_t s, const double* in, int n, double* out);
 
@@ -90,16 +97,21 @@ void build_diag(cudaStream_t s, const cplx* M11, const double* eps,
                 int ncore, int nval, int nvirt, double* diag);
 
 // ------------------------------------------------------------ Davidson
+// Arithmetic of ts_dot / ts_combine / ts_subtract: fp64 = true runs plain
+// FP64 FMAs (the FP64-class precisions); fp64 = false runs double-float
+// (float hi/lo pairs, ~48-bit significand, float exponent range) on the
+// FP32 pipes (the mixed precisions).  Both stage 16-element tiles and sum
+// the tile results in FP64.
 // out[i*ldo + j] = sum_n conj(A[i][n]) B[j][n], i < ma, j < mb
 // part must hold ma*mb*TS_CHUNKS complex.
 constexpr int TS_CHUNKS = 304;
 void ts_dot(cudaStream_t s, const cplx* A, int ma, const cplx* B, int mb,
-            int64_t N, cplx* part, cplx* out, int ldo);
+            int64_t N, cplx* part, cplx* out, int ldo, bool fp64 = false);
 // out[r][n] = sum_i W[i][n] cw[i*ldc + r] + V[i][n] cv[i*ldc + r], r < k
 // (either input may be NULL); out may not alias inputs.
 void ts_combine(cudaStream_t s, const cplx* V, const cplx* cv,
                 const cplx* W, const cplx* cw, int m, int ldc, int k,
-                int64_t N, cplx* out);
+                int64_t N, cplx* out, bool fp64 = false);
 // t[r] = (AX[r] - theta[r] X[r]) / (theta[r] - diag), |denominator|
 // clamped to >= 1e-4; rnorm2[r] = ||AX[r] - theta[r] X[r]||^2.
 void residual_precond(cudaStream_t s, const cplx* AX, const cplx* X,
@@ -108,7 +120,7 @@ void residual_precond(cudaStream_t s, const cplx* AX, const cplx* X,
 // y[r] -= sum_i V[i] c[i*ldc+r] for r < k (classical Gram-Schmidt step;
 // c laid out as ts_dot writes it)
 void ts_subtract(cudaStream_t s, const cplx* V, int m, const cplx* c,
-                 int ldc, int k, int64_t N, cplx* y);
+                 int ldc, int k, int64_t N, cplx* y, bool fp64 = false);
 // x[r] *= scale[r]
 void scale_vectors(cudaStream_t s, cplx* x, const double* scale, int k,
                    int64_t N);

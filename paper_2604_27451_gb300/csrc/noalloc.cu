@@ -73,8 +73,10 @@ extern "C" int cvsadc_zgemm_small_noalloc(void* cuda_stream, int32_t M,
     CVS_CUDA(cudaGetDevice(&dev));
     cplx* scratch = noalloc_scratch(dev);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    // the launcher splits K into at most NOALLOC_SCRATCH_ELEMS / (M N)
-    // slices, so every partial fits the array
+    // M N <= 4096 and K >= 4096 take the small-output kernel, whose
+    // launcher splits K into at most NOALLOC_SCRATCH_ELEMS / (M N) >= 128
+    // slices, so every partial fits the array; shorter K runs the tile
+    // kernel without split-K partials
     zgemm_f64(s, M, N, K, 1.0, view(A, lda, 1), view(B, ldb, 1), 0.0,
               view(C, ldc, 1), 1, scratch, NOALLOC_SCRATCH_ELEMS);
     CVS_CUDA(cudaStreamSynchronize(s));

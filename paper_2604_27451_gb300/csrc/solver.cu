@@ -155,6 +155,8 @@ struct cvsadc_ctx {
   int64_t N1 = 0, npair = 0, N2 = 0, N = 0;
   bool has_dip = false, has_fns = false;
   double emp2 = 0.0;
+  int prep_prec = 0;  // precision the prepared problem was built with
+  // t2, g2: t2 and <ab||ij> whole, [i][j][a][b]; held only when asked for
   DBuf eps, B, dip, t2, g2, M11, diag, F, fns_occ, fns_U;
   // <Kb||Ij> as h[K][b][I][j], and conj(h) as hT[(I,j,b)][K]
   DBuf h1, hT;
@@ -390,13 +392,67 @@ void build_t2(cvsadc_ctx* c, int prec, const cplx* B, const double* eps,
   c->sync();
 }
 
+// ------------------------------------------------------------ t2 in bands
+// t2 and <ab||ij> are never stored whole: every consumer (M11's Ivv, Joo and
+// K pieces, E_MP2, the transition moments, the Eq. 15 density) is a sum over
+// the first virtual index of the amplitudes, so it is accumulated band by
+// band.  A band of the first virtual index a in [a0, a0 + nb) is the GEMM
+//   X[(al, i)][(b, j)] = (a i | b j) = sum_P B^P_ai B^P_bj   (a = a0 + al),
+// laid out [al][i][b][j], which t2_band_inplace turns into
+//   G[al][i][b][j] = <ab||ij>   (in place)   and   T[al][i][b][j] = t^{ab}_{ij}.
+// Contractions over a virtual index c of t^{.c} or t^{c.} take c as the band
+// index through antisymmetry (t^{ac} = -t^{ca}).
+
+// band rows (values of the first virtual index) per band: the in-place
+// (ai|bj) block and the t2 block of each row within ~16 GB
+int band_rows(int o, int v) {
+  const double row = 2.0 * o * o * (double)v * sizeof(cplx);
+  return (int)std::max(1.0, std::min((double)v, std::floor(16e9 / row)));
+}
+
+struct Band {
+  int a0, nb;
+  const cplx* T;  // [nb][o][v][o] t^{ab}_{ij}
+  const cplx* G;  // [nb][o][v][o] <ab||ij>
+};
+
+// Runs `use` on every band of t2 built from B (o occupied and v virtual
+// spinors, L Cholesky vectors) and energies eps; returns E_MP2.
+template <class F>
+double t2_bands(cvsadc_ctx* c, int prec, const cplx* B, const double* eps, int o,
+                int v, int L, F&& use) {
+  const int n = o + v;
+  const int64_t nn = (int64_t)n * n, vo = (int64_t)v * o;
+  const int na = band_rows(o, v);
+  const int64_t nblk = t2_band_ip_blocks(na, o, v);
+  DBuf X, T, part;
+  X.ensure((size_t)na * o * vo * sizeof(cplx));
+  T.ensure((size_t)na * o * vo * sizeof(cplx));
+  part.ensure((size_t)(nblk + 1) * sizeof(double));
+  double* dE = part.d() + nblk;
+  CVS_CUDA(cudaMemsetAsync(dE, 0, sizeof(double), c->stream));
+  for (int a0 = 0; a0 < v; a0 += na) {
+    const int nb = std::min(na, v - a0);
+    View A = rows2(view(B + (int64_t)(o + a0) * n, 0, nn), n, 1, o);
+    View Bv = cols2(view(B + (int64_t)o * n, nn, 0), n, 1, o);
+    gemm(c, prec, nb * o, (int)vo, L, 1.0, A, Bv, 0.0, view(X.p, vo, 1));
+    t2_band_inplace(c->stream, X.c(), T.c(), a0, nb, o, v, eps, part.d(), dE);
+    use(Band{a0, nb, T.c(), X.c()});
+  }
+  double e = 0.0;
+  CVS_CUDA(cudaMemcpyAsync(&e, dE, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  c->sync();
+  return e;
+}
+
 // ------------------------------------------------------------------ M11
+// M11 (and, with dipoles, the transition moments through first order) of
+// the current basis, and E_MP2, from one pass over the t2 bands.
 void build_m11(cvsadc_ctx* c, int prec) {
-  const int nc = c->ncore, v = c->nvirt, o = c->o, n = c->n, L = c->naux;
-  const int64_t nn = (int64_t)n * n, N1 = c->N1;
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n, L = c->naux;
+  const int64_t nn = (int64_t)n * n, N1 = c->N1, N = c->N;
+  const int64_t vo = (int64_t)v * o, ovo = (int64_t)o * vo, vv = (int64_t)v * v;
   const cplx* B = c->B.c();
-  const cplx* t2 = c->t2.c();
-  const cplx* g2 = c->g2.c();
   c->M11.ensure(N1 * N1 * sizeof(cplx));
   size_t need = ((size_t)v * v * nc * nc + 2 * N1 * N1 + (size_t)v * v + nc * nc) *
                 sizeof(cplx);
@@ -414,60 +470,65 @@ void build_m11(cvsadc_ctx* c, int prec) {
   gemm(c, prec, (int)N1, (int)N1, L, 1.0,
        rows2(view(B + (int64_t)o * n, 0, nn), 1, n, v),
        cols2(view(B + o, nn, 0), n, 1, v), 0.0, view(C2, N1, 1));
-  const int64_t vv = (int64_t)v * v, ovv = (int64_t)o * vv;
-  // X_ab = sum_{kl,c} t^{ac}_{kl} conj(<bc||kl>)
-  gemm(c, prec, v, v, o * o * v, 1.0, cols2(view(t2, v, 0), vv, 1, v),
-       conj_of(rows2(view(g2, 0, v), vv, 1, v)), 0.0, view(X, v, 1));
-  // Y_IJ = sum_{k,cd} t^{cd}_{Ik} conj(<cd||Jk>)
-  gemm(c, prec, nc, nc, (int)ovv, 1.0, view(t2, ovv, 1),
-       conj_of(view(g2, 1, ovv)), 0.0, view(Y, nc, 1));
-  // Z_{Ia,Jb} = sum_{kc} t^{ac}_{Ik} conj(<bc||Jk>)
-  gemm(c, prec, (int)N1, (int)N1, o * v, 1.0,
-       cols2(rows2(view(t2, 0, 0), ovv, v, v), vv, 1, v),
-       conj_of(cols2(rows2(view(g2, 0, 0), vv, 1, v), ovv, v, v)), 0.0,
-       view(Z, N1, 1));
-  m11_assemble(c->stream, nc, v, o, c->eps.d(), C1, C2, X, Y, Z, 1,
-               c->M11.c());
-}
-
-// ------------------------------------------------------ transition moments
-void build_moments(cvsadc_ctx* c, int prec) {
-  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n;
-  const int64_t N1 = c->N1, N = c->N, vv = (int64_t)v * v,
-                ovv = (int64_t)o * vv;
-  const cplx* t2 = c->t2.c();
-  c->F.ensure(3 * N * sizeof(cplx));
-  size_t blk = (size_t)nc * nw * vv;
-  c->s_big2.ensure(2 * blk * sizeof(cplx));
-  cplx* tmp = c->s_big2.c();
-  cplx* T2 = tmp + blk;
-  for (int x = 0; x < 3; ++x) {
-    const cplx* d = c->dip.c() + (int64_t)x * n * n;
-    cplx* Fs = c->F.c() + (int64_t)x * N;
-    cplx* Fd = Fs + N1;
-    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 0\n", x); }
-    // F_S[I][a] = d_{aI} + sum_{kc} t^{ac}_{Ik} d_{kc}
-    copyv(c, nc, v, 1.0, view(d + (int64_t)o * n, 1, n),
-              view(Fs, v, 1));
-    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 1\n", x); }
-    gemm(c, prec, (int)N1, 1, o * v, 1.0,
-         cols2(rows2(view(t2, 0, 0), ovv, v, v), vv, 1, v),
-         rows2(view(d + o, 0, 0), n, 1, v), 1.0, view(Fs, 1, 1));
-    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 2\n", x); }
-    // tmp[I][j][a][b] = sum_c d_ac t^{cb}_{Ij}   (batched over I)
-    gemm(c, prec, v, nw * v, v, 1.0, view(d + (int64_t)o * n + o, n, 1),
-         batched(cols2(view(t2 + (int64_t)nc * vv, v, 0), vv, 1, v), ovv),
-         0.0, batched(cols2(view(tmp, v, 0), vv, 1, v), (int64_t)nw * vv), nc);
-    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 3\n", x); }
-    // T2[I][j][ab] = sum_k d_kI t^{ab}_{kj} - sum_k d_kj t^{ab}_{kI}
-    gemm(c, prec, nc, nw * (int)vv, o, 1.0, view(d, 1, n),
-         view(t2 + (int64_t)nc * vv, ovv, 1), 0.0, view(T2, nw * vv, 1));
-    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 4\n", x); }
-    gemm(c, prec, nw, nc * (int)vv, o, -1.0, view(d + nc, 1, n),
-         view(t2, ovv, 1), 1.0, cols2(view(T2, vv, 0), nw * vv, 1, (int)vv));
-    if (verbose()) { c->sync(); fprintf(stderr, "[cvsadc] moments x=%d step 5\n", x); }
-    pack_moment_doubles(c->stream, tmp, T2, nc, nw, v, Fd);
+  // transition moments: F_S starts as d_aI; the doubles pieces
+  //   A[I][j][a][b] = sum_c d_ac t^{cb}_{Ij}  and
+  //   R[I][j][a][b] = sum_k d_kI t^{ab}_{kj} - sum_k d_kj t^{ab}_{kI}
+  // accumulate over the bands, three Cartesian components at once
+  const bool mom = c->has_dip;
+  const int64_t blk = (int64_t)nc * nw * vv;
+  DBuf macc;
+  if (mom) {
+    c->F.ensure(3 * N * sizeof(cplx));
+    macc.ensure((size_t)6 * blk * sizeof(cplx));
+    for (int x = 0; x < 3; ++x)
+      copyv(c, nc, v, 1.0, view(c->dip.c() + (int64_t)x * nn + (int64_t)o * n, 1, n),
+            view(c->F.c() + (int64_t)x * N, v, 1));
   }
+  c->emp2 = t2_bands(c, prec, B, c->eps.d(), o, v, L, [&](const Band& b) {
+    const double beta = b.a0 == 0 ? 0.0 : 1.0;
+    // X_ab += sum_{(c,k),l} t^{ca}_{kl} conj(<cb||kl>)   (the Ivv piece)
+    gemm(c, prec, v, v, b.nb * o * o, 1.0, cols2(view(b.T, o, 0), vo, 1, o),
+         conj_of(rows2(view(b.G, 0, o), vo, 1, o)), beta, view(X, v, 1));
+    // Y_IJ += sum_{c,(d,k)} t^{cd}_{Ik} conj(<cd||Jk>)   (the Joo piece)
+    gemm(c, prec, nc, nc, b.nb * (int)vo, 1.0, cols2(view(b.T, vo, 0), ovo, 1, (int)vo),
+         conj_of(rows2(view(b.G, 0, vo), ovo, 1, (int)vo)), beta, view(Y, nc, 1));
+    // Z_{Ia,Jb} += sum_{c,k} t^{ca}_{Ik} conj(<cb||Jk>)   (the K piece)
+    const View Tia = cols2(rows2(view(b.T, 0, 0), vo, o, v), ovo, 1, o);
+    gemm(c, prec, (int)N1, (int)N1, b.nb * o, 1.0, Tia,
+         conj_of(cols2(rows2(view(b.G, 0, 0), ovo, 1, o), vo, o, v)), beta,
+         view(Z, N1, 1));
+    if (!mom) return;
+    for (int x = 0; x < 3; ++x) {
+      const cplx* d = c->dip.c() + (int64_t)x * nn;
+      cplx* Ax = macc.c() + (int64_t)(2 * x) * blk;
+      cplx* Rx = Ax + blk;
+      // F_S[I][a] += sum_{kc} t^{ac}_{Ik} d_kc = -sum_{c,k} t^{ca}_{Ik} d_kc
+      gemm(c, prec, (int)N1, 1, b.nb * o, -1.0, Tia,
+           rows2(view(d + o + b.a0, 0, 0), 1, n, o), 1.0,
+           view(c->F.c() + (int64_t)x * N, 1, 1));
+      // A[I][j][a][b] += sum_{c in band} d_ac t^{cb}_{Ij}   (batched over I)
+      gemm(c, prec, v, nw * v, b.nb, 1.0, view(d + (int64_t)o * n + o + b.a0, n, 1),
+           batched(cols2(view(b.T + nc, ovo, 0), 1, o, v), vo), beta,
+           batched(cols2(view(Ax, v, 0), vv, 1, v), (int64_t)nw * vv), nc);
+      // R[I][j][a][b] for a in the band (batched over a):
+      //   sum_k d_kI t^{ab}_{kj} - sum_k d_kj t^{ab}_{kI}
+      gemm(c, prec, nc, nw * v, o, 1.0, view(d, 1, n),
+           batched(cols2(view(b.T + nc, vo, 0), 1, o, v), ovo), 0.0,
+           batched(cols2(view(Rx + (int64_t)b.a0 * v, (int64_t)nw * vv, 0), vv, 1, v), v),
+           b.nb);
+      gemm(c, prec, nw, nc * v, o, -1.0, view(d + nc, 1, n),
+           batched(cols2(view(b.T, vo, 0), 1, o, v), ovo), 1.0,
+           batched(cols2(view(Rx + (int64_t)b.a0 * v, vv, 0), (int64_t)nw * vv, 1, v), v),
+           b.nb);
+    }
+  });
+  m11_assemble(c->stream, nc, v, o, c->eps.d(), C1, C2, X, Y, Z, 1, c->M11.c());
+  if (mom)
+    for (int x = 0; x < 3; ++x) {
+      const cplx* Ax = macc.c() + (int64_t)(2 * x) * blk;
+      pack_moment_doubles(c->stream, Ax, Ax + blk, nc, nw, v,
+                          c->F.c() + (int64_t)x * N + N1);
+    }
 }
 
 // ------------------------------------------------- <Kb||Ij> (1-external)
@@ -580,18 +641,17 @@ void build_fns(cvsadc_ctx* c, int prec, double tau) {
   const int n = o + v;
   (void)nc;
   (void)nw;
-  // canonical t2 (and <ab||ij>) for the density
-  DBuf t2, g2;
-  double e_can = 0.0;
-  build_t2(c, prec, c->B.c(), c->eps.d(), o, v, L, t2, g2, &e_can);
   // D_ab = 1/2 sum_{cij} t^{ac}_{ij} conj(t^{bc}_{ij})
+  //      = 1/2 sum_{c,(i,j)} t^{ca}_{ij} conj(t^{cb}_{ij})  over the bands of
+  // the canonical amplitudes
   DBuf D;
   D.ensure((size_t)v * v * sizeof(cplx));
-  const int64_t vv = (int64_t)v * v;
-  gemm(c, prec, v, v, o * o * v, 0.5, cols2(view(t2.p, v, 0), vv, 1, v),
-       conj_of(rows2(view(t2.p, 0, v), vv, 1, v)), 0.0, view(D.p, v, 1));
-  t2.release();
-  g2.release();
+  const int64_t vv = (int64_t)v * v, vo = (int64_t)v * o;
+  t2_bands(c, prec, c->B.c(), c->eps.d(), o, v, L, [&](const Band& b) {
+    gemm(c, prec, v, v, b.nb * o * o, 0.5, cols2(view(b.T, o, 0), vo, 1, o),
+         conj_of(rows2(view(b.T, 0, o), vo, 1, o)), b.a0 == 0 ? 0.0 : 1.0,
+         view(D.p, v, 1));
+  });
   // Hermitian part for the eigensolver
   DBuf A, Vec, w;
   A.ensure(vv * sizeof(cplx));
@@ -715,8 +775,11 @@ void validate(const cvsadc_params* p) {
               CVSADC_EINVAL, "problem too large");
 }
 
+// keep_t2: also store t2 and <ab||ij> whole (o^2 v^2 each; the gradient's
+// reverse pass reads them)
 void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
-                  const void* B, const void* dip, cvsadc_info* info) {
+                  const void* B, const void* dip, cvsadc_info* info,
+                  bool keep_t2 = false) {
   validate(p);
   CVS_REQUIRE(eps && B, CVSADC_EINVAL, "eps and B are required");
   double t0 = now_ms();
@@ -738,7 +801,13 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   check_hermitian(c, c->B.c(), n, c->naux, "B");
   if (c->has_dip) check_hermitian(c, c->dip.c(), n, 3, "dip");
   c->has_fns = p->fns_threshold > 0;
+  // the problem (FNS, t2, M11, couplings, moments) is built at the requested
+  // precision, except for BF16X3, whose accumulation-limited products
+  // (~1e-5 relative) would leave M itself ~1e-4 Eh off: its problem is built
+  // with the FP64-class 7-slice product and BF16X3 runs the Davidson sigma
   int prec = p->precision;
+  if (prec == CVSADC_MIXED_BF16X3)
+    prec = tc_available() ? CVSADC_FP64_SLICE7 : CVSADC_FP64;
   if (c->has_fns) {
     build_fns(c, prec, p->fns_threshold);
     set_sizes(c);
@@ -750,17 +819,19 @@ void prepare_impl(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
       fprintf(stderr, "[cvsadc] %-8s %10.2f ms\n", what, now_ms() - t);
     }
   };
+  c->prep_prec = prec;
+  c->t2.release();
+  c->g2.release();
   double ts = now_ms();
-  build_t2(c, prec, c->B.c(), c->eps.d(), c->o, c->nvirt, c->naux, c->t2, c->g2,
-           &c->emp2);
-  stage("t2", ts);
+  build_m11(c, prec);  // with E_MP2 and, with dipoles, the moments
+  stage("t2+m11", ts);
   ts = now_ms();
-  build_m11(c, prec);
   build_h(c, prec);
-  stage("m11", ts);
-  ts = now_ms();
-  if (c->has_dip) build_moments(c, prec);
-  stage("moments", ts);
+  if (keep_t2) {
+    double e = 0.0;
+    build_t2(c, prec, c->B.c(), c->eps.d(), c->o, c->nvirt, c->naux, c->t2, c->g2, &e);
+  }
+  stage("h", ts);
   c->diag.ensure(c->N * sizeof(double));
   build_diag(c->stream, c->M11.c(), c->eps.d(), c->ncore, c->nval, c->nvirt,
              c->diag.d());
@@ -1156,6 +1227,9 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
                         cplx* Xout, double* wout,
                         bool stop_on_stagnation = false, bool schur = false) {
   schur = schur && c->sch_on;
+  // Gram matrices, Gram-Schmidt and Ritz combinations: plain FP64 for the
+  // FP64-class precisions, double-float on the FP32 pipes for the mixed ones
+  const bool a64 = prec == CVSADC_FP64 || prec == CVSADC_FP64_SLICE7;
   const int64_t N = c->N;
   const int k = nroots;
   const int msub = std::max(max_sub, 2 * k + 2);
@@ -1237,22 +1311,22 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
   auto orthonormalise_append = [&](cplx* T, int cnt) {
     cnt = std::min(cnt, msub - m);
     if (cnt <= 0) return 0;
-    ts_dot(s, T, cnt, T, cnt, N, part, G0, cnt);
+    ts_dot(s, T, cnt, T, cnt, N, part, G0, cnt, a64);
     gram_diag_sqrt(s, G0, cnt, cnt, nrm0);
     if (m > 0) {
       for (int pass = 0; pass < 2; ++pass) {
-        ts_dot(s, V, m, T, cnt, N, part, Cproj, cnt);
-        ts_subtract(s, V, m, Cproj, cnt, cnt, N, T);
+        ts_dot(s, V, m, T, cnt, N, part, Cproj, cnt, a64);
+        ts_subtract(s, V, m, Cproj, cnt, cnt, N, T, a64);
       }
     }
-    ts_dot(s, T, cnt, T, cnt, N, part, G0, cnt);
+    ts_dot(s, T, cnt, T, cnt, N, part, G0, cnt, a64);
     block_orth(s, G0, cnt, cnt, nrm0, 1e-8, Xo, kept_d);
     int kept = 0;
     CVS_CUDA(cudaMemcpyAsync(&kept, kept_d, sizeof(int), cudaMemcpyDeviceToHost, s));
     c->sync();
     if (kept > 0)
       ts_combine(s, T, Xo, nullptr, nullptr, cnt, cnt, kept, N,
-                 V + (int64_t)m * N);
+                 V + (int64_t)m * N, a64);
     m += kept;
     return kept;
   };
@@ -1279,7 +1353,7 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     res.sigmas += nnew;
     // subspace matrix columns for the new vectors
     ts_dot(s, V, m, W + (int64_t)m_done * N, nnew, N, part,
-           c->dv_H.c() + m_done, msub);
+           c->dv_H.c() + m_done, msub, a64);
     // the new rows against the old sigma images follow from Hermiticity
     herm_fill(s, c->dv_H.c(), msub, m_done, m);
     m_done = m;
@@ -1288,8 +1362,8 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     jacobi_eigh(s, c->dv_A.c(), m, c->dv_w.d(), c->dv_U.c(), 60,
                 dwork + W_JAC);
     // Ritz vectors and their sigma images for the lowest k
-    ts_combine(s, V, c->dv_U.c(), nullptr, nullptr, m, m, k, N, c->dv_X.c());
-    ts_combine(s, nullptr, nullptr, W, c->dv_U.c(), m, m, k, N, c->dv_AX.c());
+    ts_combine(s, V, c->dv_U.c(), nullptr, nullptr, m, m, k, N, c->dv_X.c(), a64);
+    ts_combine(s, nullptr, nullptr, W, c->dv_U.c(), m, m, k, N, c->dv_AX.c(), a64);
     residual_precond(s, c->dv_AX.c(), c->dv_X.c(), c->dv_w.d(),
                      schur ? nullptr : c->diag.d(), k, N, c->dv_T.c(),
                      dwork + W_PART, dwork + W_RN2);
@@ -1342,8 +1416,8 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
     // not fit
     if (m + (int)todo.size() > msub) {
       const int nk = std::min(nkeep, m);
-      ts_combine(s, V, c->dv_U.c(), nullptr, nullptr, m, m, nk, N, c->dv_X.c());
-      ts_combine(s, nullptr, nullptr, W, c->dv_U.c(), m, m, nk, N, c->dv_AX.c());
+      ts_combine(s, V, c->dv_U.c(), nullptr, nullptr, m, m, nk, N, c->dv_X.c(), a64);
+      ts_combine(s, nullptr, nullptr, W, c->dv_U.c(), m, m, nk, N, c->dv_AX.c(), a64);
       CVS_CUDA(cudaMemcpyAsync(V, c->dv_X.p, (size_t)nk * N * sizeof(cplx),
                                cudaMemcpyDeviceToDevice, s));
       CVS_CUDA(cudaMemcpyAsync(W, c->dv_AX.p, (size_t)nk * N * sizeof(cplx),
@@ -1506,7 +1580,7 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
     // T_n^x = X_n^H F^x, f_n = 2/3 w_n sum_x |T|^2
     cplx* part = c->dv_misc.c();
     cplx* Tn = part + (size_t)k * 3 * TS_CHUNKS;
-    ts_dot(c->stream, Xd.c(), k, c->F.c(), 3, c->N, part, Tn, 3);
+    ts_dot(c->stream, Xd.c(), k, c->F.c(), 3, c->N, part, Tn, 3, true);
     std::vector<cplx> T((size_t)k * 3);
     CVS_CUDA(cudaMemcpyAsync(T.data(), Tn, T.size() * sizeof(cplx),
                              cudaMemcpyDeviceToHost, c->stream));
@@ -1755,7 +1829,7 @@ void grad_entry(cvsadc_ctx* c, const cvsadc_params* p, const double* eps,
   cvsadc_params q = *p;
   q.precision = CVSADC_FP64;
   q.flags = (p->flags & CVSADC_FLAG_DEVICE_PTRS);
-  prepare_impl(c, &q, eps, B, nullptr, nullptr);
+  prepare_impl(c, &q, eps, B, nullptr, nullptr, true);
   const int k = q.nroots;
   CVS_REQUIRE(k >= 1 && k <= 64 && k <= c->N, CVSADC_EINVAL, "bad nroots");
   const double tol = p->conv_residual > 0 ? p->conv_residual : 1e-8;
@@ -1822,8 +1896,8 @@ int guarded(cvsadc_ctx* c, F&& f) {
 // ------------------------------------------------------ batched solves
 namespace {
 
-// Device bytes one solve of `p` holds at its peak: inputs, t2 and <ab||ij>,
-// the (ai|bj) band, M11 and its build scratch, the Davidson subspace and
+// Device bytes one solve of `p` holds at its peak: inputs, the t2 band
+// buffers, the moment accumulators, M11 and its build scratch, the Davidson subspace and
 // block vectors, the sigma intermediates of its largest block (the initial
 // guesses), the tensor-core packing workspace of the largest contraction
 // and the split-K scratch.  Host arithmetic only; used to admit instances
@@ -1843,10 +1917,12 @@ double estimate_bytes(const cvsadc_params* p) {
   if (schur_on) g = std::max(g, std::min<double>(SCHUR_P, N1));
   double b = 8 * n + z * L * n * n;
   b += 3 * z * n * n;                       // dipoles
-  b += 2 * z * o * o * v * v;               // t2, <ab||ij>
-  if (p->fns_threshold > 0) b += 2 * z * o * o * v * v + 2 * z * v * v;
-  const double band = std::min(4.0 * (1 << 30), z * o * v * o * v);
-  b += std::max(band, z * g * N1 * wv);     // s_big1
+  // t2 bands: the in-place (ai|bj) / <ab||ij> block and the t2 block
+  const double band = std::min(16e9, 2 * z * o * o * v * v);
+  b += band;
+  b += 6 * z * nc * nw * v * v;             // moment accumulators (with dipoles)
+  if (p->fns_threshold > 0) b += z * L * n * n + 2 * z * v * v;  // rotated B^P
+  b += z * g * N1 * wv;                     // s_big1
   b += std::max({z * (v * v * nc * nc + 2 * N1 * N1 + v * v + nc * nc),
                  z * g * N1 * wv, 2 * z * nc * nw * v * v});  // s_big2
   b += z * N1 * N1 + 8 * N;                 // M11, diagonal
@@ -1863,7 +1939,7 @@ double estimate_bytes(const cvsadc_params* p) {
       return (double)(nsl ? slice_workspace_bytes((int)M, (int)Nn, (int)K, nsl)
                           : tc_workspace_bytes((int)M, (int)Nn, (int)K, 3));
     };
-    const double na = std::max(1.0, std::min(v, std::floor(band / (z * o * v * o))));
+    const double na = std::max(1.0, std::min(v, std::floor(band / (2 * z * o * v * o))));
     double w = 0;
     for (double s : {ws(na * o, v * o, L, ns), ws(N1, N1, L, ns), ws(N1, N1, o * v, ns),
                      ws(g * N1, L, wv, ns), ws(g * wv, L, N1, ns), ws(g * N1, wv, L, ns),
@@ -2103,9 +2179,16 @@ int cvsadc_get_t2(cvsadc_ctx* c, int32_t flags, void* t2, double* emp2) {
   return guarded(c, [&] {
     CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
     if (emp2) *emp2 = c->emp2;
-    if (t2)
+    if (t2) {
+      // built on request: the prepared problem does not keep t2 whole
+      if (!c->t2.p) {
+        double e = 0.0;
+        build_t2(c, c->prep_prec, c->B.c(), c->eps.d(), c->o, c->nvirt, c->naux,
+                 c->t2, c->g2, &e);
+      }
       download(c, t2, c->t2.p, (size_t)c->o * c->o * c->nvirt * c->nvirt * sizeof(cplx),
                flags & CVSADC_FLAG_DEVICE_PTRS);
+    }
     c->sync();
   });
 }
@@ -2223,6 +2306,25 @@ int cvsadc_zgemm(cvsadc_ctx* c, int32_t precision, int32_t flags, int32_t M,
            view(pc, ldc, 1));
     }
     if (!dev) download(c, C, dc.p, cb, false);
+    c->sync();
+  });
+}
+
+int cvsadc_block_dot(cvsadc_ctx* c, int32_t precision, const void* A,
+                     int32_t ma, const void* B, int32_t mb, int64_t N, void* out) {
+  if (!c || !A || !B || !out || ma < 1 || mb < 1 || N < 1) return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    CVS_REQUIRE(valid_precision(precision), CVSADC_EINVAL, "unknown precision");
+    const size_t ab = (size_t)ma * N * sizeof(cplx), bb = (size_t)mb * N * sizeof(cplx);
+    RegGuard ga(A, ab), gb(B, bb);
+    const bool f64 = precision == CVSADC_FP64 || precision == CVSADC_FP64_SLICE7;
+    DBuf part, o;
+    part.ensure((size_t)std::min(ma, 96) * std::min(mb, 192) * TS_CHUNKS * sizeof(cplx) +
+                (size_t)ma * mb * sizeof(cplx));
+    o.ensure((size_t)ma * mb * sizeof(cplx));
+    ts_dot(c->stream, (const cplx*)A, ma, (const cplx*)B, mb, N, part.c(), o.c(), mb, f64);
+    CVS_CUDA(cudaMemcpyAsync(out, o.p, (size_t)ma * mb * sizeof(cplx),
+                             cudaMemcpyDeviceToHost, c->stream));
     c->sync();
   });
 }

@@ -190,8 +190,9 @@ def test_mixed_solve_refined_matches_oracle():
     ctx = pkg.Context(0)
     out = ctx.solve(inst.eps, inst.B, inst.dip, nc, nw, nv, 3, precision="bf16x3",
                     conv=1e-7, refine_sweeps=6)
-    # BF16X3 carries ~1e-5 relative GEMM error (accumulation-limited); the
-    # FP64 correction sweeps bring the roots back within the 1e-4 Eh band
-    # here, and the exact-slice modes above are the ones that meet 1e-5
-    assert np.abs(out["omega"] - w_ref).max() < 2e-4
+    # BF16X3 carries ~1e-5 relative GEMM error (accumulation-limited) in the
+    # Davidson sigma only: the problem is built with the FP64-class product,
+    # so the FP64-class correction sweeps converge to the right matrix's
+    # roots
+    assert np.abs(out["omega"] - w_ref).max() < 1e-5
     ctx.close()

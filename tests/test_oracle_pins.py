@@ -131,6 +131,25 @@ def test_t2_antisymmetry_and_density():
     assert abs(np.trace(D) - 0.5 * np.sum(np.abs(t) ** 2)) < 1e-13 * abs(np.trace(D))
 
 
+def test_density_orientation_from_exact_ground_state(tiny):
+    """Eq. 15's D_ab is the lambda^2 coefficient of the exact ground state's
+    <a_b^+ a_a> (the density whose eigenvectors, as columns, are the natural
+    spinors of Eqs. 17-20).  Trace, Hermiticity and positivity hold for D and
+    D^T alike; this fixes which one the oracle builds: the lambda^2
+    coefficient of <a_a^+ a_b> must equal D^T, and must differ from D."""
+    inst, isr, cM, cF, cE = tiny
+    nc, nw, nv = inst.ncore, inst.nval, inst.nvirt
+    o = nc + nw
+    D = mp2.density_vv(inst.eps, inst.B, nc, nw, nv)
+    g = isr.ground_rdm1_taylor()
+    gvv = g[2][o:, o:]  # lambda^2 coefficient of <a_a^+ a_b>, a, b virtual
+    scale = np.abs(D).max()
+    assert np.abs(g[1][o:, o:]).max() < 1e-9 * scale  # no first-order vv density
+    assert np.abs(gvv - D.T).max() < 1e-7 * scale
+    # negative control: the other orientation is measurably different
+    assert np.abs(gvv - D).max() > 1e-3 * scale
+
+
 # ------------------------------------------------------- T3 ISR brute force
 
 def _blocks(inst):

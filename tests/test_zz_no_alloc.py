@@ -3,9 +3,12 @@
 For callers that must not let the library allocate device memory (their
 memory is owned by another allocator, or cudaMalloc's synchronisation is
 not acceptable).  Through the C ABI it must give what the allocating entry
-point cvsadc_zgemm (FP64) gives, within the FP64 tolerance of the other
-GEMM tests (1e-13 of |A||B|), on two calls in a row with different inputs
--- the second call would expose state left in the shared scratch array.
+point cvsadc_zgemm (FP64) gives, and what a complex128 product on the CPU
+gives, within the FP64 tolerance of the other GEMM tests (1e-13 of
+|A||B|), on two calls in a row with different inputs -- the second call
+would expose state left in the shared scratch array.  The long-K shape
+takes the small-output kernel with as many K slices as the fixed array
+holds.
 This file is collected last so that a failure here leaves every other test
 already run; it also passes alone in a fresh process.
 """
@@ -17,7 +20,8 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(6, 300, 20000), (40, 100, 5000), (17, 13, 70001), (64, 64, 300)]
+SHAPES = [(6, 300, 20000), (40, 100, 5000), (17, 13, 70001), (64, 64, 300),
+          (64, 64, 300000)]
 
 
 def _call(lib, stream, A, B, C):
@@ -47,10 +51,13 @@ def test_noalloc_matches_allocating_entry_point(shape):
                        device="cuda")
         assert _call(lib, stream, A, B, C) == 0
         ref = ctx.zgemm(A, B, "fp64")
+        cpu = A.cpu().numpy() @ B.cpu().numpy()
         bound = (A.abs() @ B.abs()).cpu().numpy()
-        err = (C - ref).abs().cpu().numpy() / bound
-        assert np.isfinite(err).all()
-        assert err.max() < 1e-13, (call, err.max())
+        Cn = C.cpu().numpy()
+        for want in (ref.cpu().numpy(), cpu):
+            err = np.abs(Cn - want) / bound
+            assert np.isfinite(err).all()
+            assert err.max() < 1e-13, (call, err.max())
     ctx.close()
 
 
