@@ -2,23 +2,24 @@
 
 Metric: CVS-ADC(2) sigma builds/s and time-to-roots, mixed vs FP64.
 
-Timed step: one sigma build M x over a block of 8 trial vectors (the
-Davidson block of the 8-root medium workload: ncore 6, nval 60, nvirt 300,
-naux 1500; N = 16 147 800 CVS-packed amplitudes per vector) through the
-full sigma path -- doubles unpack, the four B^P coupling GEMMs per vector,
-the small B^P contractions, M22 applied on the fly, CVS packing, the dense
-M11 x1 -- in the mixed precision (tensor-core exact-slice GEMMs, SLICE4),
-with the problem prepared on the device (t2, M11, moments) and the inputs
-(B^P, 3.2 GB, larger than L2) resident in HBM.  value = sigma builds per
-second over all ranks.
+Timed step: one sigma build M x over a block of 4 trial vectors of the
+large workload (two metal L-edges: ncore 12, nval 120, nvirt 600, naux
+3000, 16 roots; N = 258 775 200 CVS-packed amplitudes, 4.14 GB per
+complex128 vector) through the full sigma path -- doubles unpack, the
+B^P coupling GEMMs, the <Kb||Ij> terms through the stored 1-external
+block, M22 applied on the fly, CVS packing, the dense M11 x1 -- in the
+mixed precision (tensor-core exact-slice GEMMs, SLICE4), with the problem
+prepared on the device (t2 bands, M11) and the inputs (B^P, 25.7 GB,
+larger than L2) resident in HBM.  value = sigma builds per second over all
+ranks.
 
-Also reported on the same line: sigma builds/s of every precision, the
-time-to-roots of full solves on the small workload (mixed vs FP64, and
-their root difference), the e2e sigma rate through the C ABI with host
-buffers, the roofline of the tcgen05 slice GEMM from CUDA-event timing of
-its launches inside the timed region, SM clocks sampled during the timed
-region, and a CPU baseline (the oracle's matrix-free sigma on a bounded
-sample of the same workload).
+Also reported on the same line: sigma builds/s of the other precisions,
+time-to-roots of full solves (mixed vs FP64-class, and their root
+difference) on the small, medium and large workloads, the e2e sigma rate
+through the C ABI with host buffers, the roofline of the tcgen05 slice GEMM
+from CUDA-event timing of its launches inside the timed region, SM clocks
+sampled during the timed region, and a CPU baseline (the oracle's
+matrix-free sigma on a bounded sample of the same workload).
 
 --impl reference times that CPU oracle alone (the reference arm).
 Multi-GPU (torchrun): independent replicas, one per GPU (weak scaling).
@@ -45,20 +46,27 @@ from synth import WORKLOADS, make_instance  # noqa: E402
 
 METRIC = "CVS-ADC(2) sigma builds/s and time-to-roots, mixed vs FP64 (≤1e-5 Eh), 1 GB300"
 UNIT = "sigma builds/s"
-WORKLOAD = "medium"
-NVEC = 8
+WORKLOAD = "large"
+NVEC = 4
 PRODUCTS = {"slice4": 10, "fp64_slice7": 28, "bf16x3": 3}
+
+
+def n_amplitudes(w):
+    return w["ncore"] * w["nvirt"] + w["ncore"] * w["nval"] * w["nvirt"] * (w["nvirt"] - 1) // 2
 
 
 def workload_config(prec):
     w = WORKLOADS[WORKLOAD]
+    n = w["ncore"] + w["nval"] + w["nvirt"]
     return {
-        "workload": "medium CVS-ADC(2): ncore %d, nval %d, nvirt %d, naux %d, %d roots; "
+        "workload": "%s CVS-ADC(2): ncore %d, nval %d, nvirt %d, naux %d, %d roots; "
                     "sigma on %d-vector Davidson blocks" % (
-                        w["ncore"], w["nval"], w["nvirt"], w["naux"], w["nroots"], NVEC),
+                        WORKLOAD, w["ncore"], w["nval"], w["nvirt"], w["naux"], w["nroots"],
+                        NVEC),
         "precision": prec,
-        "n_amplitudes": w["ncore"] * w["nvirt"] + w["ncore"] * w["nval"] * w["nvirt"] * (w["nvirt"] - 1) // 2,
-        "l2": "inputs larger than L2 (B^P 3.2 GB, trial block 2.1 GB)",
+        "n_amplitudes": n_amplitudes(w),
+        "l2": "inputs larger than L2 (B^P %.1f GB, trial block %.1f GB)" % (
+            w["naux"] * n * n * 16 / 1e9, NVEC * n_amplitudes(w) * 16 / 1e9),
         "inputs": "seeded synthetic (synth.make_instance, seed 0)",
     }
 
@@ -172,38 +180,71 @@ def traffic_from_profile():
 
 # --------------------------------------------------------- CPU baseline
 
-def cpu_baseline(inst, seconds_hint=20.0):
-    """The oracle's matrix-free sigma on one valence-spinor block of the
-    workload (1/nval of the coupling work), scaled to sigma builds/s."""
-    from oracle import adc2
+class OracleSigmaSample:
+    """The oracle's matrix-free sigma of one vector in bounded units: a unit
+    is the coupling block of one valence spinor j (explicit <ab||cj>)
+    restricted to `rows` values of the first virtual index; nval x
+    ceil(nvirt / rows) units plus one whole-vector doubles unpack and pack
+    make one sigma build."""
 
-    nc, nw, nv = inst.ncore, inst.nval, inst.nvirt
-    N1, _, N2 = adc2.sizes(nc, nw, nv)
-    # the dense M11 x1 product is N1^2 (3.2M) multiply-adds, negligible next
-    # to the couplings; a zero M11 keeps the sample to the coupling work
-    sig = adc2.Sigma(inst.eps, inst.B, nc, nw, nv, M11=np.zeros((N1, N1), complex),
-                     cache_blocks=False)
-    rng = np.random.default_rng(1)
-    x = rng.standard_normal(N1 + N2) + 1j * rng.standard_normal(N1 + N2)
+    def __init__(self, inst, rows):
+        from oracle import adc2
+
+        self.adc2 = adc2
+        nc, nw, nv = inst.ncore, inst.nval, inst.nvirt
+        self.nw, self.nv, self.rows = nw, nv, min(rows, nv)
+        N1, _, N2 = adc2.sizes(nc, nw, nv)
+        # the dense M11 x1 product is N1^2 multiply-adds, negligible next to
+        # the couplings; a zero M11 keeps the oracle from building it
+        self.sig = adc2.Sigma(inst.eps, inst.B, nc, nw, nv,
+                              M11=np.zeros((N1, N1), complex), cache_blocks=False)
+        rng = np.random.default_rng(1)
+        x = rng.standard_normal(N1 + N2) + 1j * rng.standard_normal(N1 + N2)
+        self.X = x[:N1].reshape(nc, nv)
+        t0 = time.perf_counter()
+        self.Y = adc2.unpack(x[N1:], nc, nw, nv)
+        s2 = np.zeros((nc, nw, nv, nv), dtype=np.complex128)
+        adc2.pack(s2, nv)
+        self.t_vector = time.perf_counter() - t0
+        self.nslice = (nv + self.rows - 1) // self.rows
+        self.units = nw * self.nslice
+        self.i = 0
+
+    def unit(self):
+        j, q = divmod(self.i % self.units, self.nslice)
+        r = slice(q * self.rows, min(self.nv, (q + 1) * self.rows))
+        self.sig.coupling_block(self.X, self.Y, j, r)
+        self.i += 1
+
+    def rate(self, t_unit):
+        """sigma builds/s from the mean time of one unit."""
+        return 1.0 / (self.t_vector + self.units * t_unit)
+
+
+def cpu_baseline(inst, seconds_hint=20.0, rows=None):
+    """The oracle's matrix-free sigma, timed on a bounded sample of units
+    (see OracleSigmaSample), scaled to one sigma build."""
+    smp = OracleSigmaSample(inst, rows or inst.nvirt)
     t0 = time.perf_counter()
-    nblk = 0
+    n = 0
     while True:
-        sig(x[:N1], x[N1:], jlist=[nblk % nw])
-        nblk += 1
-        if time.perf_counter() - t0 > seconds_hint or nblk >= nw:
+        smp.unit()
+        n += 1
+        if time.perf_counter() - t0 > seconds_hint or n >= smp.units:
             break
     dt = time.perf_counter() - t0
-    per_sigma = dt / nblk * nw
     try:
         import threadpoolctl
 
         cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or os.cpu_count()
     except Exception:
         cores = os.cpu_count()
-    return {"value": 1.0 / per_sigma, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "oracle matrix-free sigma (explicit <ab||cj> per valence spinor) on "
-                      "%d of %d valence blocks of the medium workload, one vector, "
-                      "scaled x%d; %.1f s of CPU work" % (nblk, nw, nw, dt)}
+    return {"value": smp.rate(dt / n), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "oracle matrix-free sigma (explicit <ab||cj> per valence spinor) of the "
+                      "%s workload, one vector: %d of %d units (valence spinor x %d rows "
+                      "of the first virtual index) in %.1f s, scaled to all units, plus one "
+                      "whole-vector doubles unpack and pack (%.1f s)" % (
+                          WORKLOAD, n, smp.units, smp.rows, dt, smp.t_vector)}
 
 
 # ------------------------------------------------------------- our arm
@@ -230,12 +271,14 @@ def run_ours(args):
     ctx = pkg.Context(local, stream=stream.cuda_stream)
     eps = torch.from_numpy(inst.eps).to(dev)
     B = torch.from_numpy(inst.B).to(dev)
-    dip = torch.from_numpy(inst.dip).to(dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx.prepare(eps, B, dip, nc, nw, nv, precision=prec)
+    # sigma needs no transition moments: prepared without dipoles
+    ctx.prepare(eps, B, None, nc, nw, nv, precision=prec)
     torch.cuda.synchronize()
     prepare_s = time.perf_counter() - t0
+    del B  # the library holds its own copy of B^P
+    torch.cuda.empty_cache()
     N = ctx.shape["N"]
     g = torch.Generator(device=dev).manual_seed(11)
     X = torch.randn(NVEC, N, dtype=torch.complex128, device=dev, generator=g)
@@ -311,7 +354,9 @@ def run_ours(args):
         "clocks": clk.summary(), "roofline": roofline,
     }
     if rank == 0 and not args.core_only:
-        out.update(extras(args, ctx, inst, X, S, stream, torch, pkg, (eps, B, dip)))
+        state = {"ctx": ctx, "X": X, "S": S}
+        del X, S
+        out.update(extras(args, state, inst, stream, torch, pkg))
     elif rank == 0:
         out["e2e"] = None
     if rank == 0:
@@ -323,11 +368,18 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def extras(args, ctx, inst, X, S, stream, torch, pkg, dev_inputs):
+def extras(args, state, inst, stream, torch, pkg):
+    """Everything on the JSON line besides the timed step.  state holds the
+    prepared context and the trial block; both are released before the full
+    solves so that those start from an empty device."""
     res = {}
-    # sigma builds/s of every precision on the same block
+    ctx, X = state["ctx"], state["X"]
+    dev = X.device
+    # sigma builds/s of the other precisions on (part of) the same block;
+    # FP64 FMA runs at ~1.1 TFLOP/s on this GPU: one vector is minutes at the
+    # large workload, so it is timed on the medium solve below instead
     rates = {}
-    for p, nvec in (("bf16x3", NVEC), ("slice4", NVEC), ("fp64_slice7", NVEC), ("fp64", 1)):
+    for p, nvec in (("bf16x3", NVEC), ("slice4", NVEC), ("fp64_slice7", 2)):
         xs = X[:nvec].contiguous()
         ss = torch.empty_like(xs)
         ctx.sigma(xs, p, out=ss)
@@ -339,6 +391,7 @@ def extras(args, ctx, inst, X, S, stream, torch, pkg, dev_inputs):
         e1.record(stream)
         torch.cuda.synchronize()
         rates[p] = round(nvec / (e0.elapsed_time(e1) / 1e3), 3)
+        del xs, ss
     res["sigma_builds_per_s"] = rates
     # e2e: the public API with host buffers (pinned), copies inside
     N = X.shape[1]
@@ -356,6 +409,13 @@ def extras(args, ctx, inst, X, S, stream, torch, pkg, dev_inputs):
     res["e2e"] = {"value": round(NVEC / dt, 3), "unit": UNIT, "h2d_bytes_per_step": nb,
                   "d2h_bytes_per_step": nb,
                   "path": "cvsadc_sigma through the C ABI with pinned host buffers"}
+    del xh, sh, xn, sn
+    state.clear()
+    del X
+    ctx.close()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
     # time-to-roots: full solves (prepare + Davidson + refinement) with
     # inputs resident, mixed vs FP64; the Schur-complement preconditioner
     # is on unless the entry says "diag"
@@ -375,7 +435,6 @@ def extras(args, ctx, inst, X, S, stream, torch, pkg, dev_inputs):
             "schur_builds": i["schur_builds"], "t_schur_s": round(i["t_schur_ms"] / 1e3, 3),
             "t_prepare_s": round(i["t_prepare_ms"] / 1e3, 3)}
 
-    dev = X.device
     w = WORKLOADS["small"]
     sm = make_instance(w["ncore"], w["nval"], w["nvirt"], w["naux"], seed=0)
     e_, B_, d_ = (torch.from_numpy(a).to(dev) for a in (sm.eps, sm.B, sm.dip))
@@ -390,23 +449,27 @@ def extras(args, ctx, inst, X, S, stream, torch, pkg, dev_inputs):
     ttr["max_abs_root_diff_fp64_slice7_vs_fp64_Eh"] = float(np.abs(roots["fp64_slice7"] - roots["fp64"]).max())
     ttr["speedup_mixed_vs_fp64"] = round(ttr["fp64"]["s"] / ttr["slice4"]["s"], 2)
     res["time_to_roots"] = ttr
-    # the medium workload (the one the sigma rate is quoted on)
-    wm = WORKLOADS[WORKLOAD]
+    del e_, B_, d_
+    # the medium workload: mixed vs FP64-class (7-slice) time-to-roots
+    wm = WORKLOADS["medium"]
+    me = make_instance(wm["ncore"], wm["nval"], wm["nvirt"], wm["naux"], seed=0)
+    e_, B_, d_ = (torch.from_numpy(a).to(dev) for a in (me.eps, me.B, me.dip))
     ttm = {"workload": "medium CVS-ADC(2): ncore %d, nval %d, nvirt %d, naux %d, %d roots, "
                        "residual 1e-6, inputs resident" % (
                            wm["ncore"], wm["nval"], wm["nvirt"], wm["naux"], wm["nroots"])}
     rm = {}
-    rm["slice4"], ttm["slice4"] = solve_entry(dev_inputs[0], dev_inputs[1], dev_inputs[2], wm,
-                                              "slice4", conv=1e-6)
-    if args.ttr_medium_fp64:
-        rm["fp64"], ttm["fp64"] = solve_entry(dev_inputs[0], dev_inputs[1], dev_inputs[2], wm,
-                                              "fp64", conv=1e-6)
-        ttm["max_abs_root_diff_mixed_vs_fp64_Eh"] = float(np.abs(rm["slice4"] - rm["fp64"]).max())
-        ttm["speedup_mixed_vs_fp64"] = round(ttm["fp64"]["s"] / ttm["slice4"]["s"], 2)
+    for p in ("slice4", "fp64_slice7") + (("fp64",) if args.ttr_medium_fp64 else ()):
+        rm[p], ttm[p] = solve_entry(e_, B_, d_, wm, p, conv=1e-6)
+    for p in rm:
+        if p != "slice4":
+            ttm["max_abs_root_diff_slice4_vs_%s_Eh" % p] = float(np.abs(rm["slice4"] - rm[p]).max())
+            ttm["speedup_slice4_vs_%s" % p] = round(ttm[p]["s"] / ttm["slice4"]["s"], 2)
     ttm["roots_Eh"] = [round(float(x), 9) for x in rm["slice4"]]
     res["time_to_roots_medium"] = ttm
+    del e_, B_, d_, me
+    torch.cuda.empty_cache()
     if not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds)
+        res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds, rows=max(1, inst.nvirt // 8))
     return res
 
 
@@ -418,24 +481,35 @@ def run_reference(args):
         return
     w = WORKLOADS[WORKLOAD]
     inst = make_instance(w["ncore"], w["nval"], w["nvirt"], w["naux"], seed=0)
-    seconds = max(2.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    # one step = one unit of the oracle's sigma: a valence spinor's coupling
+    # block on a slice of rows, sized to a few seconds
+    smp = OracleSigmaSample(inst, max(1, w["nvirt"] // 24))
     for _ in range(args.warmup):
-        cpu_baseline(inst, seconds)
-    vals = []
+        smp.unit()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(inst, seconds))
+        smp.unit()
     dt = time.perf_counter() - t0
-    v = statistics.mean(x["value"] for x in vals)
-    cb = dict(vals[-1])
-    cb["value"] = v
-    out = {"metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": ws,
+    v = smp.rate(dt / args.steps)
+    try:
+        import threadpoolctl
+
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or os.cpu_count()
+    except Exception:
+        cores = os.cpu_count()
+    cb = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": "oracle matrix-free sigma of the %s workload, one vector: each step one "
+                    "unit (a valence spinor's <ab||cj> coupling block on %d rows of the "
+                    "first virtual index, %d units per sigma), scaled, plus one whole-vector "
+                    "doubles unpack and pack (%.1f s)" % (WORKLOAD, smp.rows, smp.units,
+                                                           smp.t_vector)}
+    out = {"metric": METRIC, "value": round(v, 8), "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
            "config": workload_config("fp64 (CPU oracle)"), "impl": "reference",
            "cpu_baseline": cb,
-           "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+           "e2e": {"value": round(v, 8), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -201,15 +201,37 @@ class Sigma:
         self.cache_blocks = cache_blocks
         self._vvv = {}
 
-    def block(self, j):
-        """<ab||cj> for valence spinor j, as [a, b, c]."""
-        if j in self._vvv:
+    def block(self, j, rows=None):
+        """<ab||cj> for valence spinor j, as [a, b, c] (a over `rows`, a
+        slice of the virtual indices, default all)."""
+        if rows is None and j in self._vvv:
             return self._vvv[j]
         C, W, O, V = _idx(self.ncore, self.nval, self.nvirt)
-        g = antisym(self.B, V, V, V, W[j:j + 1])[..., 0]
-        if self.cache_blocks:
+        Va = V if rows is None else V[rows]
+        g = antisym(self.B, Va, V, V, W[j:j + 1])[..., 0]
+        if self.cache_blocks and rows is None:
             self._vvv[j] = g
         return g
+
+    def coupling_block(self, X, Y, j, rows=None):
+        """Valence spinor j's share of the couplings, from X = x1 as [K, c]
+        and Y = the unpacked doubles [I, j, a, b]: (M21 x1)[:, j] as [I, a, b]
+        and its term of M12 x2 as [K, c].  With `rows` (a slice of the first
+        virtual index a) only those rows of (M21 x1)[:, j] and their part of
+        the M12 x2 sum are formed: a bounded piece of the same work."""
+        g = self.block(j, rows)
+        h = self.cvcw
+        ra = slice(None) if rows is None else rows
+        # M21 x1
+        s2j = (-np.einsum("abc,Ic->Iab", g, X)
+               + np.einsum("KbI,Ka->Iab", h[:, :, :, j], X[:, ra])
+               - np.einsum("KaI,Kb->Iab", h[:, ra, :, j], X))
+        # M12 x2 = sum over a<b of conj(M21) x2 = 1/2 over all a, b; the
+        # <ab||cj> term sums over the rows a, the <Kb||Ij> term fills the
+        # columns c in the rows
+        s1j = -0.5 * np.einsum("abc,Kab->Kc", np.conj(g), Y[:, j, ra])
+        s1j[:, ra] += np.einsum("KbI,Icb->Kc", np.conj(h[:, :, :, j]), Y[:, j, ra])
+        return s2j, s1j
 
     def __call__(self, x1, x2, jlist=None):
         nc, nw, nv = self.ncore, self.nval, self.nvirt
@@ -217,17 +239,10 @@ class Sigma:
         Y = unpack(x2, nc, nw, nv)  # [I, j, a, b]
         s1 = (self.M11 @ x1).reshape(nc, nv)
         s2 = np.zeros((nc, nw, nv, nv), dtype=np.complex128)
-        h = self.cvcw
         jl = range(nw) if jlist is None else jlist
         for j in jl:
-            g = self.block(j)
-            # M21 x1
-            s2[:, j] = (-np.einsum("abc,Ic->Iab", g, X)
-                        + np.einsum("KbI,Ka->Iab", h[:, :, :, j], X)
-                        - np.einsum("KaI,Kb->Iab", h[:, :, :, j], X))
-            # M12 x2 = sum over a<b of conj(M21) x2 = 1/2 over all a, b
-            s1 += -0.5 * np.einsum("abc,Kab->Kc", np.conj(g), Y[:, j])
-            s1 += np.einsum("KbI,Icb->Kc", np.conj(h[:, :, :, j]), Y[:, j])
+            s2[:, j], s1j = self.coupling_block(X, Y, j)
+            s1 += s1j
         s2 = pack(s2, nv) + self.d22 * x2
         return s1.reshape(-1), s2
 

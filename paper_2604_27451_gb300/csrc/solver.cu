@@ -591,10 +591,13 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
     gemm(c, prec, (int)(g * N1), L, (int)wv, 1.0, view(Yt, wv, 1),
          rows2(view(B + (int64_t)nc * n + o, 0, nn), n, 1, v), 0.0,
          view(S, L, 1));
-    // sigma1 (M12 x2), the <ab||cj> part: rows (q, K), columns c
+    // sigma1 (M12 x2), the <ab||cj> part, transposed so that the long side
+    // (c) is the row dimension: sigma1^T[c][(q, K)] = -sum_{(a,P)} B^P_ca
+    // S[(q,K,a)][P]
     const View s1rows = rows2(view(sig, 0, 1), N, v, nc);
-    gemm(c, prec, g * nc, v, (int)vL, -1.0, view(S, vL, 1),
-         rows2(view(B + (int64_t)o * n + o, 0, n), 1, nn, L), 0.0, s1rows);
+    gemm(c, prec, v, g * nc, (int)vL, -1.0,
+         cols2(view(B + (int64_t)o * n + o, n, 0), 1, nn, L), trans(view(S, vL, 1)),
+         0.0, trans(s1rows));
     // the <Kb||Ij> part: sigma1[K][c] += sum_{Ijb} y_{Ijcb} conj(h[K][b][I][j]),
     // rows (q, c), columns K
     const View s1t = rows2(view(sig, 0, v), N, 1, v);  // ((q,c), K)
@@ -603,10 +606,11 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
          view(c->hT.c(), nc, 1), 1.0, s1t);
   }
   if (mode == SIG_ADJ) return;
-  // Y[(q,I,a)][P] = sum_c x_Ic B^P_ac
-  gemm(c, prec, g * nc, (int)vL, v, 1.0, rows2(view(x, 0, 1), N, v, nc),
-       cols2(view(B + (int64_t)o * n + o, 1, 0), n, nn, L), 0.0,
-       view(Y, vL, 1));
+  // Y[(q,I,a)][P] = sum_c x_Ic B^P_ac, as its transpose
+  // Y^T[(a,P)][(q,I)] = sum_c B^P_ac x_Ic (the long side (a, P) as rows)
+  gemm(c, prec, (int)vL, g * nc, v, 1.0,
+       rows2(view(B + (int64_t)o * n + o, 0, 1), n, nn, L),
+       trans(rows2(view(x, 0, 1), N, v, nc)), 0.0, trans(view(Y, vL, 1)));
   // G[q][(I,a)][(j,b)] = sum_P Y B^P_{bj} (the <ab||cj> part of M21 x1; the
   // <Kb||Ij> part is added while packing)
   gemm(c, prec, (int)(g * N1), (int)wv, L, 1.0, view(Y, L, 1),
