@@ -91,6 +91,10 @@ extern "C" {
 #define CVSADC_FLAG_RETURN_X 2     /* write eigenvectors to X */
 #define CVSADC_FLAG_NO_REFINE 4    /* mixed path: skip the FP64 residual
                                       correction sweep */
+#define CVSADC_FLAG_FOLDED 16      /* the doubles-folded solver (singles-
+                                      space vectors only; see cvsadc_solve);
+                                      chosen without this flag when the
+                                      full-space subspace would not fit */
 #define CVSADC_FLAG_DIAG_PRECOND 8 /* Davidson with the diagonal
                                       preconditioner only (no Schur
                                       complement) */

@@ -15,8 +15,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (  # noqa: F401
-    CVSADC_FLAG_DEVICE_PTRS, CVSADC_FLAG_DIAG_PRECOND, CVSADC_FLAG_NO_REFINE,
-    CVSADC_FLAG_RETURN_X,
+    CVSADC_FLAG_DEVICE_PTRS, CVSADC_FLAG_DIAG_PRECOND, CVSADC_FLAG_FOLDED,
+    CVSADC_FLAG_NO_REFINE, CVSADC_FLAG_RETURN_X,
     CVSADC_FP64, CVSADC_MIXED_BF16X3, CVSADC_ENOTCONV, Info, Params,
 )
 
@@ -221,11 +221,13 @@ class Context:
         return out
 
     def davidson(self, nroots, precision="fp64", conv=1e-6, max_iter=0,
-                 max_subspace=0, return_x=False, refine=True, precond="schur"):
+                 max_subspace=0, return_x=False, refine=True, precond="schur",
+                 solver="auto"):
         s = self._shape
         flags = (CVSADC_FLAG_DIAG_PRECOND if precond == "diag" else 0) | \
             (CVSADC_FLAG_RETURN_X if return_x else 0) | \
-            (0 if refine else CVSADC_FLAG_NO_REFINE)
+            (0 if refine else CVSADC_FLAG_NO_REFINE) | \
+            (CVSADC_FLAG_FOLDED if solver == "folded" else 0)
         p = self.params(s["ncore"], s["nval"], s["nvirt"], s["naux"], nroots,
                         precision, 0.0, conv, max_iter, max_subspace, flags)
         omega = np.empty(nroots)
@@ -268,8 +270,9 @@ class Context:
 
     def solve(self, eps, B, dip, ncore, nval, nvirt, nroots, precision="fp64",
               tau=0.0, conv=1e-6, max_iter=0, max_subspace=0, return_x=False,
-              refine=True, refine_sweeps=0, precond="schur"):
-        """The whole path through cvsadc_solve."""
+              refine=True, refine_sweeps=0, precond="schur", solver="auto"):
+        """The whole path through cvsadc_solve.  solver: "auto" (the library
+        picks), or "folded" (the doubles-folded solver)."""
         naux = B.shape[0]
         _inputs_ready(eps, B, dip)
         pe, dev = _ptr(eps)
@@ -278,7 +281,8 @@ class Context:
         flags = (CVSADC_FLAG_DEVICE_PTRS if dev else 0) | \
             (CVSADC_FLAG_RETURN_X if return_x else 0) | \
             (0 if refine else CVSADC_FLAG_NO_REFINE) | \
-            (CVSADC_FLAG_DIAG_PRECOND if precond == "diag" else 0)
+            (CVSADC_FLAG_DIAG_PRECOND if precond == "diag" else 0) | \
+            (CVSADC_FLAG_FOLDED if solver == "folded" else 0)
         p = self.params(ncore, nval, nvirt, naux, nroots, precision, tau, conv,
                         max_iter, max_subspace, flags, refine_sweeps)
         if dev:

@@ -31,6 +31,7 @@ CVSADC_FLAG_DEVICE_PTRS = 1
 CVSADC_FLAG_RETURN_X = 2
 CVSADC_FLAG_NO_REFINE = 4
 CVSADC_FLAG_DIAG_PRECOND = 8
+CVSADC_FLAG_FOLDED = 16
 
 
 class Params(ctypes.Structure):

@@ -783,7 +783,7 @@ __global__ void hermitize_kernel(const cplx* H, int ldh, int m, int jdone,
 // X[j][q] (leading dimension cnt) holds kept column q; *kept = their count.
 __global__ void block_orth_kernel(const cplx* G, int ldg, int cnt,
                                   const double* norm0, double tol, cplx* X,
-                                  int* kept) {
+                                  int* kept, int* src) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int nk = 0;
   cplx u[64], gu[64];
@@ -813,6 +813,7 @@ __global__ void block_orth_kernel(const cplx* G, int ldg, int cnt,
     double nrm = sqrt(fmax(nrm2, 0.0));
     if (nrm > tol * norm0[j] && nrm > 1e-300) {
       for (int a = 0; a < cnt; ++a) X[a * cnt + nk] = cscale(u[a], 1.0 / nrm);
+      if (src) src[nk] = j;
       ++nk;
     }
   }
@@ -1111,9 +1112,10 @@ void herm_fill(cudaStream_t s, cplx* H, int ldh, int i0, int i1) {
 }
 
 void block_orth(cudaStream_t s, const cplx* G, int ldg, int cnt,
-                const double* norm0, double tol, cplx* X, int* kept) {
+                const double* norm0, double tol, cplx* X, int* kept, int* src) {
   CVS_REQUIRE(cnt >= 1 && cnt <= 64, -1, "block_orth: at most 64 vectors");
-  block_orth_kernel<<<1, 32, 0, s>>>(G, ldg, cnt, norm0, tol, X, kept);
+  CVS_REQUIRE(cnt >= 1 && cnt <= 64, -1, "block_orth: block of 1..64 vectors");
+  block_orth_kernel<<<1, 32, 0, s>>>(G, ldg, cnt, norm0, tol, X, kept, src);
   CVS_CHECK_LAUNCH();
 }
 

@@ -139,8 +139,11 @@ void hermitize(cudaStream_t s, const cplx* H, int ldh, int m, cplx* A,
 // H[i][j] = conj(H[j][i]) for i0 <= i < i1, j < i0
 void herm_fill(cudaStream_t s, cplx* H, int ldh, int i0, int i1);
 // transform X (cnt x kept) making the block with Gram matrix G orthonormal
+// (Gram-Schmidt in coefficient space, cnt <= 64); src[q] (optional) = the
+// input vector kept column q was started from
 void block_orth(cudaStream_t s, const cplx* G, int ldg, int cnt,
-                const double* norm0, double tol, cplx* X, int* kept);
+                const double* norm0, double tol, cplx* X, int* kept,
+                int* src = nullptr);
 void gram_diag_sqrt(cudaStream_t s, const cplx* G, int ldg, int cnt,
                     double* out);
 // X[r][c] *= sc[r] (device scale vector)
@@ -200,6 +203,17 @@ void eig_shift(cudaStream_t s, cplx* Y, int64_t n1, int k, const double* lam,
                const double* theta);
 void diag_precond(cudaStream_t s, const cplx* r, double theta,
                   const double* diag, int64_t N, cplx* out);
+// folded solver (see lift_assemble_kernel in schur_kernels.cu)
+void lift_assemble(cudaStream_t s, const cplx* E, const cplx* VD, const cplx* A,
+                   const cplx* VV, const double* th, int m, int ld, double delta,
+                   cplx* Q, cplx* H, cplx* O);
+void lift_coef(cudaStream_t s, const cplx* C, int m, int k, int ldc, const double* w,
+               const double* th, cplx* Cp);
+void row_axpy(cudaStream_t s, const cplx* X, const cplx* Z, const double* w, int k,
+              int64_t n, cplx* Y);
+void row_norm2(cudaStream_t s, const cplx* X, int k, int64_t n, double* out);
+void inv_sqrt_cols(cudaStream_t s, const cplx* U, const double* w, int m, int off, int kept,
+                   int ldu, cplx* Oi);
 void add_singles(cudaStream_t s, const cplx* a, const cplx* b, int64_t N,
                  int64_t n1, int k, cplx* out);
 

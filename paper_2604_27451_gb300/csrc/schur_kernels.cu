@@ -434,7 +434,124 @@ __global__ void add_singles_kernel(const cplx* __restrict__ a,
   }
 }
 
+// Projected matrices of the folded solver's lifted basis z_j = (v_j,
+// W_j M21 v_j), W_j = (theta_j - M22)^-1, from singles-space products:
+//   E = V^H R (R_j = M12 W_j M21 v_j), VD = V^H D (D_j = M12 W_j^2 M21 v_j),
+//   A = V^H M11 V, VV = V^H V  (all m x m, leading dimension ld).
+// Doubles overlap Q_ij = (W_i M21 v_i)^H (W_j M21 v_j):
+//   |theta_i - theta_j| > delta: partial fractions,
+//     Q_ij = (E_ij - conj(E_ji)) / (theta_i - theta_j);
+//   otherwise the midpoint (W_i W_j = (W_i^2 + W_j^2)/2 + O(dtheta^2)),
+//     Q_ij = (VD_ij + conj(VD_ji)) / 2.
+// Then H = A + E + Q diag(theta) and O = VV + Q, both Hermitised.
+__global__ void lift_assemble_kernel(const cplx* __restrict__ E,
+                                     const cplx* __restrict__ VD,
+                                     const cplx* __restrict__ A,
+                                     const cplx* __restrict__ VV,
+                                     const double* __restrict__ th, int m, int ld,
+                                     double delta, cplx* __restrict__ Q,
+                                     cplx* __restrict__ H, cplx* __restrict__ O) {
+  const int total = m * m;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e / m, j = e % m;
+    auto q = [&](int a, int b) {
+      const double dt = th[a] - th[b];
+      if (fabs(dt) > delta)
+        return cscale(csub(E[a * ld + b], cconj(E[b * ld + a])), 1.0 / dt);
+      return cscale(cadd(VD[a * ld + b], cconj(VD[b * ld + a])), 0.5);
+    };
+    // Hermitian by construction up to rounding: average (i,j) and (j,i)
+    const cplx qij = cscale(cadd(q(i, j), cconj(q(j, i))), 0.5);
+    const cplx hij = cadd(cadd(A[i * ld + j], E[i * ld + j]), cscale(q(i, j), th[j]));
+    const cplx hji = cadd(cadd(A[j * ld + i], E[j * ld + i]), cscale(q(j, i), th[i]));
+    Q[i * ld + j] = qij;
+    H[i * ld + j] = cscale(cadd(hij, cconj(hji)), 0.5);
+    O[i * ld + j] = cadd(cscale(cadd(VV[i * ld + j], cconj(VV[j * ld + i])), 0.5), qij);
+  }
+}
+
+// Cp[j][q] = C[j][q] (w[q] - th[j]), j < m, q < k (leading dimensions ldc)
+__global__ void lift_coef_kernel(const cplx* __restrict__ C, int m, int k, int ldc,
+                                 const double* __restrict__ w,
+                                 const double* __restrict__ th, cplx* __restrict__ Cp) {
+  const int total = m * k;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int j = e / k, q = e % k;
+    Cp[j * ldc + q] = cscale(C[j * ldc + q], w[q] - th[j]);
+  }
+}
+
+// Y[q][s] = X[q][s] - w[q] Z[q][s] for k rows of n
+__global__ void row_axpy_kernel(const cplx* __restrict__ X, const cplx* __restrict__ Z,
+                                const double* __restrict__ w, int k, int64_t n,
+                                cplx* __restrict__ Y) {
+  const int q = blockIdx.y;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = (int64_t)q * n + s;
+    const cplx z = Z[e];
+    Y[e] = cmake(X[e].x - w[q] * z.x, X[e].y - w[q] * z.y);
+  }
+}
+
+// out[q] = sum_s |X[q][s]|^2 (FP64), one block per row
+__global__ void row_norm2_kernel(const cplx* __restrict__ X, int64_t n,
+                                 double* __restrict__ out) {
+  const int q = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t s = threadIdx.x; s < n; s += blockDim.x) {
+    const cplx x = X[(int64_t)q * n + s];
+    acc += x.x * x.x + x.y * x.y;
+  }
+  acc = sum_block(acc);
+  if (threadIdx.x == 0) out[q] = acc;
+}
+
+// Oi[i][c] = U[i][off + c] / sqrt(w[off + c]), i < m, c < kept (ld ldu)
+__global__ void inv_sqrt_cols_kernel(const cplx* __restrict__ U, const double* __restrict__ w,
+                                     int m, int off, int kept, int ldu,
+                                     cplx* __restrict__ Oi) {
+  const int total = m * kept;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int i = e / kept, cc = e % kept;
+    Oi[i * ldu + cc] = cscale(U[i * ldu + off + cc], 1.0 / sqrt(w[off + cc]));
+  }
+}
+
 }  // namespace
+
+void lift_assemble(cudaStream_t s, const cplx* E, const cplx* VD, const cplx* A,
+                   const cplx* VV, const double* th, int m, int ld, double delta,
+                   cplx* Q, cplx* H, cplx* O) {
+  lift_assemble_kernel<<<grid1d((int64_t)m * m, 128), 128, 0, s>>>(E, VD, A, VV, th, m, ld,
+                                                                    delta, Q, H, O);
+  CVS_CHECK_LAUNCH();
+}
+
+void lift_coef(cudaStream_t s, const cplx* C, int m, int k, int ldc, const double* w,
+               const double* th, cplx* Cp) {
+  lift_coef_kernel<<<grid1d((int64_t)m * k, 128), 128, 0, s>>>(C, m, k, ldc, w, th, Cp);
+  CVS_CHECK_LAUNCH();
+}
+
+void row_axpy(cudaStream_t s, const cplx* X, const cplx* Z, const double* w, int k,
+              int64_t n, cplx* Y) {
+  dim3 grid(grid1d(n, 256, 304), k);
+  row_axpy_kernel<<<grid, 256, 0, s>>>(X, Z, w, k, n, Y);
+  CVS_CHECK_LAUNCH();
+}
+
+void row_norm2(cudaStream_t s, const cplx* X, int k, int64_t n, double* out) {
+  row_norm2_kernel<<<k, 256, 0, s>>>(X, n, out);
+  CVS_CHECK_LAUNCH();
+}
+
+void inv_sqrt_cols(cudaStream_t s, const cplx* U, const double* w, int m, int off, int kept,
+                   int ldu, cplx* Oi) {
+  inv_sqrt_cols_kernel<<<grid1d((int64_t)m * kept, 128), 128, 0, s>>>(U, w, m, off, kept,
+                                                                        ldu, Oi);
+  CVS_CHECK_LAUNCH();
+}
 
 void h_assemble(cudaStream_t s, const cplx* hc1, const cplx* hc2, int nc,
                 int nw, int nv, cplx* h) {

@@ -167,6 +167,10 @@ struct cvsadc_ctx {
   DBuf err;  // device int: non-zero after a bounded device wait expired
   DBuf s_kpart;  // split-K partial products
 
+  // folded solver: fold work vectors [2g][N] x 2, singles-space basis and
+  // its folds [msub][N1], small projected matrices
+  DBuf fd_A, fd_B, fd_th, fv_V, fv_B, fv_R, fv_D, fv_MV, fv_T, fv_T2, fv_small;
+
   // Schur-complement preconditioner of the prepared problem
   DBuf sch_W, sch_g, sch_S, sch_U, sch_V, sch_lam, sch_C11, sch_C12, sch_work,
       sch_tmp, sch_th;
@@ -197,7 +201,8 @@ struct cvsadc_ctx {
             &s_part, &s_small, &s_tc, &dv_V, &dv_W, &dv_X, &dv_AX, &dv_T,
             &dv_H,  &dv_A,  &dv_U,  &dv_w, &dv_misc, &sch_W, &sch_g,
             &sch_S, &sch_U, &sch_V, &sch_lam, &sch_C11, &sch_C12, &sch_work,
-            &sch_tmp, &sch_th};
+            &sch_tmp, &sch_th, &fd_A, &fd_B, &fd_th, &fv_V, &fv_B, &fv_R, &fv_D,
+            &fv_MV, &fv_T, &fv_T2, &fv_small};
   }
   // give back every problem-sized buffer (the context stays usable)
   void trim() {
@@ -1550,6 +1555,520 @@ DavResult solve_roots(cvsadc_ctx* c, int prec, int k, double tol, int max_iter,
   return r;
 }
 
+// ===================================================== doubles-folded solver
+// M22 is diagonal, so an eigenpair (omega, z) of M with omega below the
+// lowest M22 entry has z = (x1, W(omega) M21 x1), W(theta) = (theta -
+// M22)^-1, where x1 solves the pseudo-eigenvalue problem S(omega) x1 =
+// omega x1 with S(theta) = M11 + M12 W(theta) M21 (Eqs. 11-12; exact because
+// the doubles block is diagonal).  This solver stores singles-space vectors
+// only.  Its basis vectors are lifts z_j = (v_j, W_j M21 v_j), each at its
+// own theta_j, represented by v_j and the two folds
+//   R_j = M12 W_j M21 v_j   and   D_j = M12 W_j^2 M21 v_j,
+// from which every projected matrix of M over the basis follows exactly
+// (lift_assemble): the Rayleigh-Ritz step is the one of M in the full
+// space, and no doubles vector outlives a fold.  A Ritz pair (omega, C) has
+// the full residual r = (sum_j c_j (s_j - omega v_j),
+// sum_j c_j (theta_j - omega) W_j u_j), s_j = M11 v_j + R_j, whose norm
+// also follows from the projected matrices, and the folded residual
+// r~ = S(omega) x1 - omega x1 ~ sum_j c_j (s_j - (omega - theta_j) D_j -
+// omega v_j).  New directions are preconditioned folded residuals lifted at
+// the current Ritz values; lifts made at outdated theta leave a part of the
+// residual that singles directions cannot remove, so once ||r~|| falls
+// below half of ||r|| the basis restarts from the Ritz singles lifted at
+// their Ritz values.
+
+// R = M12 W M21 v and D = M12 W^2 M21 v for b singles vectors (rows of V,
+// [b][N1]) with theta th[b] (host); R and D are [b][N1].  Each group of g
+// vectors goes through one forward coupling product (M21), two weightings
+// and one adjoint product (M12) over 2g vectors.
+void fold_apply(cvsadc_ctx* c, int prec, const cplx* V, int b, const double* th,
+                cplx* R, cplx* D) {
+  const int64_t N = c->N, N1 = c->N1;
+  cudaStream_t s = c->stream;
+  const double per = 4.0 * (double)N * sizeof(cplx);
+  const int g = (int)std::max(1.0, std::min((double)b, 40e9 / per));
+  c->fd_A.ensure((size_t)2 * g * N * sizeof(cplx));
+  c->fd_B.ensure((size_t)2 * g * N * sizeof(cplx));
+  c->fd_th.ensure((size_t)(2 * g + 8) * sizeof(double));
+  for (int q0 = 0; q0 < b; q0 += g) {
+    const int gg = std::min(g, b - q0);
+    cplx* X = c->fd_A.c();   // [gg][N] lift input, later [2gg][N] adjoint output
+    cplx* Sg = X + (int64_t)gg * N;
+    cplx* U2 = c->fd_B.c();  // [2gg][N]: (0, W u) then (0, W^2 u)
+    CVS_CUDA(cudaMemsetAsync(X, 0, (size_t)gg * N * sizeof(cplx), s));
+    copyv(c, gg, (int)N1, 1.0, view(V + (int64_t)q0 * N1, N1, 1), view(X, N, 1));
+    sigma_impl(c, prec, X, Sg, gg, SIG_FWD);  // doubles of Sg = M21 v
+    CVS_CUDA(cudaMemcpyAsync(c->fd_th.p, th + q0, gg * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    fold_doubles(s, Sg, nullptr, c->fd_th.d(), gg, N, N1, c->ncore, c->nval, c->nvirt,
+                 c->eps.d(), true, U2);
+    fold_doubles(s, U2, nullptr, c->fd_th.d(), gg, N, N1, c->ncore, c->nval, c->nvirt,
+                 c->eps.d(), true, U2 + (int64_t)gg * N);
+    sigma_impl(c, prec, U2, X, 2 * gg, SIG_ADJ);  // singles of X = M12 (.)
+    copyv(c, gg, (int)N1, 1.0, view(X, N, 1), view(R + (int64_t)q0 * N1, N1, 1));
+    copyv(c, gg, (int)N1, 1.0, view(X + (int64_t)gg * N, N, 1),
+          view(D + (int64_t)q0 * N1, N1, 1));
+    c->sync();  // fd_th is reused by the next group
+  }
+  c->sch_couplings += 3 * b;
+}
+
+struct FoldResult {
+  int iters = 0, folds = 0, restarts = 0, converged = 0;
+  double maxres = 0.0;
+};
+
+// Lowest k roots by the doubles-folded solver in precision `prec`.  Starting
+// singles x0 [nx0][N1] at theta th0 (host), or (nx0 == 0) the lowest
+// eigenvectors of the Schur preconditioner S(theta0).  Outputs: the Ritz
+// singles X1 [k][N1] (device) and the roots w[k] (host).
+FoldResult folded_davidson(cvsadc_ctx* c, int prec, int k, int max_iter, int max_sub,
+                           double tol, const cplx* x0, const double* th0, int nx0,
+                           cplx* X1out, double* wout, bool stop_on_stagnation,
+                           bool newton_start) {
+  const int64_t N1 = c->N1;
+  cudaStream_t s = c->stream;
+  const bool a64 = prec == CVSADC_FP64 || prec == CVSADC_FP64_SLICE7;
+  const int msub = std::min(128, std::max(max_sub, 3 * k + 2));
+  const double delta = 1e-3;  // partial fractions vs midpoint rule for Q
+  FoldResult res;
+  c->fv_V.ensure((size_t)msub * N1 * sizeof(cplx));
+  c->fv_B.ensure((size_t)msub * N1 * sizeof(cplx));
+  c->fv_R.ensure((size_t)msub * N1 * sizeof(cplx));
+  c->fv_D.ensure((size_t)msub * N1 * sizeof(cplx));
+  c->fv_MV.ensure((size_t)msub * N1 * sizeof(cplx));
+  c->fv_T.ensure((size_t)4 * k * N1 * sizeof(cplx));
+  c->fv_T2.ensure((size_t)4 * k * N1 * sizeof(cplx));
+  // small device matrices (leading dimension msub, or the block size for
+  // the orthonormalisation scratch, up to 64)
+  const size_t mm = (size_t)std::max(msub, 64) * std::max(msub, 64);
+  const size_t n_small = 13 * mm;
+  const size_t W_PART = n_small * 2;  // in doubles
+  const size_t TSP = (size_t)std::min(msub, 96) * 192 * TS_CHUNKS;
+  c->fv_small.ensure(n_small * sizeof(cplx) + TSP * sizeof(cplx) +
+                     (size_t)(6 * msub + 4096) * sizeof(double));
+  cplx* E = c->fv_small.c();
+  cplx* VD = E + mm;
+  cplx* Am = VD + mm;
+  cplx* VV = Am + mm;
+  cplx* Q = VV + mm;
+  cplx* H = Q + mm;
+  cplx* O = H + mm;
+  cplx* Uo = O + mm;
+  cplx* Oi = Uo + mm;
+  cplx* Hp = Oi + mm;
+  cplx* Yp = Hp + mm;
+  cplx* C = Yp + mm;
+  cplx* Cp = C + mm;
+  cplx* tsp = c->fv_small.c() + n_small;
+  double* dw = (double*)(tsp + TSP);
+  double* wo = dw;              // [msub]
+  double* wp = wo + msub;       // [msub]
+  double* thd = wp + msub;      // [msub]
+  double* rn1 = thd + msub;     // [msub]
+  double* rnt = rn1 + msub;     // [msub]
+  double* jinfo = rnt + msub;   // jacobi info + misc
+  cplx* V = c->fv_V.c();
+  cplx* Bo = c->fv_B.c();  // orthonormal basis of span(V) (singles metric)
+  cplx* Rf = c->fv_R.c();
+  cplx* Df = c->fv_D.c();
+  cplx* MV = c->fv_MV.c();
+  cplx* T = c->fv_T.c();
+  cplx* T2 = c->fv_T2.c();
+  std::vector<double> th(msub, 0.0);
+  int m = 0, nb = 0;  // basis size, orthonormal-basis size
+
+  // orthonormal rows of T (cnt) against Bo[0:nb] and within, appended to
+  // Bo and (when toV) V; returns how many were kept
+  double* nrm0 = jinfo + 16;
+  int* kept_d = (int*)(jinfo + 16 + 256);
+  int* src_d = kept_d + 64;
+  std::vector<int> src_h(64);
+  cplx* G0 = Hp;  // scratch for the block Gram / transform (cnt <= 4k <= msub)
+  cplx* Xo = Yp;
+  auto orth_append = [&](cplx* Tb, int cnt, bool toV) {
+    if (cnt <= 0) return 0;
+    ts_dot(s, Tb, cnt, Tb, cnt, N1, tsp, G0, cnt, a64);
+    gram_diag_sqrt(s, G0, cnt, cnt, nrm0);
+    if (nb > 0)
+      for (int pass = 0; pass < 2; ++pass) {
+        ts_dot(s, Bo, nb, Tb, cnt, N1, tsp, Cp, cnt, a64);
+        ts_subtract(s, Bo, nb, Cp, cnt, cnt, N1, Tb, a64);
+      }
+    ts_dot(s, Tb, cnt, Tb, cnt, N1, tsp, G0, cnt, a64);
+    block_orth(s, G0, cnt, cnt, nrm0, 1e-10, Xo, kept_d, src_d);
+    int kept = 0;
+    CVS_CUDA(cudaMemcpyAsync(&kept, kept_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemcpyAsync(src_h.data(), src_d, 64 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    c->sync();
+    kept = std::min(kept, msub - nb);
+    if (kept > 0) {
+      ts_combine(s, Tb, Xo, nullptr, nullptr, cnt, cnt, kept, N1, Bo + (int64_t)nb * N1, a64);
+      if (toV)
+        CVS_CUDA(cudaMemcpyAsync(V + (int64_t)m * N1, Bo + (int64_t)nb * N1,
+                                 (size_t)kept * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    }
+    nb += kept;
+    return kept;
+  };
+  // lift rows [m0, m0 + cnt) of V at th[m0..], fold, and M11 V
+  auto lift = [&](int m0, int cnt) {
+    fold_apply(c, prec, V + (int64_t)m0 * N1, cnt, th.data() + m0, Rf + (int64_t)m0 * N1,
+               Df + (int64_t)m0 * N1);
+    gemm64(c, cnt, (int)N1, (int)N1, 1.0, view(V + (int64_t)m0 * N1, N1, 1),
+           trans(view(c->M11.c(), N1, 1)), 0.0, view(MV + (int64_t)m0 * N1, N1, 1));
+    res.folds += cnt;
+  };
+  // set the basis to the rows of Xs (cnt, normalised) lifted at ths
+  auto restart = [&](const cplx* Xs, const double* ths, int cnt) {
+    cnt = std::min(cnt, msub);
+    CVS_CUDA(cudaMemcpyAsync(V, Xs, (size_t)cnt * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    row_norm2(s, V, cnt, N1, rn1);
+    std::vector<double> nn(cnt), sc(cnt);
+    CVS_CUDA(cudaMemcpyAsync(nn.data(), rn1, cnt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    c->sync();
+    for (int q = 0; q < cnt; ++q) sc[q] = nn[q] > 0 ? 1.0 / std::sqrt(nn[q]) : 1.0;
+    CVS_CUDA(cudaMemcpyAsync(rn1, sc.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+    scale_vectors(s, V, rn1, cnt, N1);
+    for (int q = 0; q < cnt; ++q) th[q] = ths[q];
+    m = cnt;
+    lift(0, cnt);
+    // orthonormal basis of the restart singles
+    nb = 0;
+    CVS_CUDA(cudaMemcpyAsync(T2, V, (size_t)cnt * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    for (int q0 = 0; q0 < cnt; q0 += 64) orth_append(T2 + (int64_t)q0 * N1, std::min(64, cnt - q0), false);
+    ++res.restarts;
+  };
+
+  // ---- initial basis
+  int nguess;
+  if (x0 && nx0 > 0) {
+    nguess = std::min(nx0, msub);
+    restart(x0, th0, nguess);
+    --res.restarts;
+  } else {
+    CVS_REQUIRE(c->sch_on, CVSADC_EINVAL, "folded solver: no initial vectors");
+    // the lowest eigenvectors of S(theta0), lifted at theta0
+    nguess = (int)std::min<int64_t>(std::min(2 * k, msub), N1);
+    copyv(c, nguess, (int)N1, 1.0, view(c->sch_U.c(), 1, N1), view(T, N1, 1));
+    std::vector<double> t0(nguess, c->sch_theta);
+    restart(T, t0.data(), nguess);
+    --res.restarts;
+    newton_start = true;
+  }
+  if (newton_start) {
+    // one Newton step on each starting vector u lifted at theta,
+    // omega ~ theta + (lam - theta) / (1 + ||W M21 u||^2) (the Rayleigh
+    // quotient of the lift), gives the theta it is lifted at next
+    ts_dot(s, V, m, Rf, m, N1, tsp, E, msub, a64);
+    ts_dot(s, V, m, MV, m, N1, tsp, Am, msub, a64);
+    ts_dot(s, V, m, Df, m, N1, tsp, VD, msub, a64);
+    std::vector<cplx> he((size_t)m * msub), ha((size_t)m * msub), hd((size_t)m * msub);
+    CVS_CUDA(cudaMemcpyAsync(he.data(), E, he.size() * sizeof(cplx), cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemcpyAsync(ha.data(), Am, ha.size() * sizeof(cplx), cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemcpyAsync(hd.data(), VD, hd.size() * sizeof(cplx), cudaMemcpyDeviceToHost, s));
+    c->sync();
+    std::vector<double> est(m);
+    for (int q = 0; q < m; ++q) {
+      const double lam = he[(size_t)q * msub + q].x + ha[(size_t)q * msub + q].x;
+      const double nq = hd[(size_t)q * msub + q].x;
+      est[q] = th[q] + (lam - th[q]) / (1.0 + nq);
+      if (!std::isfinite(est[q])) est[q] = th[q];
+    }
+    CVS_CUDA(cudaMemcpyAsync(T, V, (size_t)m * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    restart(T, est.data(), m);
+    --res.restarts;
+  }
+
+  std::vector<double> w(msub), r1(k), rt(k), hist;
+  std::vector<cplx> g2((size_t)k * k);
+  for (int it = 0; it < max_iter; ++it) {
+    // projected matrices over the lifted basis
+    CVS_CUDA(cudaMemcpyAsync(thd, th.data(), m * sizeof(double), cudaMemcpyHostToDevice, s));
+    ts_dot(s, V, m, Rf, m, N1, tsp, E, msub, a64);
+    ts_dot(s, V, m, MV, m, N1, tsp, Am, msub, a64);
+    ts_dot(s, V, m, Df, m, N1, tsp, VD, msub, a64);
+    ts_dot(s, V, m, V, m, N1, tsp, VV, msub, a64);
+    lift_assemble(s, E, VD, Am, VV, thd, m, msub, delta, Q, H, O);
+    // generalised eigenproblem H c = w O c through O^-1/2 (eigenvalues of O
+    // below 1e-12 of the largest are dropped)
+    hermitize(s, O, msub, m, Hp, m);
+    jacobi_eigh(s, Hp, m, wo, Uo, 60, jinfo);
+    std::vector<double> hw(m);
+    CVS_CUDA(cudaMemcpyAsync(hw.data(), wo, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    c->sync();
+    int off = 0;
+    while (off < m - 1 && !(hw[off] > 1e-12 * hw[m - 1])) ++off;
+    const int kept = m - off;
+    // Uo is [m][m] dense (ld m); Oi [m][kept] with ld msub
+    inv_sqrt_cols(s, Uo, wo, m, off, kept, m, Oi);
+    // Hp = Oi^H H Oi (kept x kept)
+    gemm64(c, m, kept, m, 1.0, view(H, msub, 1), view(Oi, m, 1), 0.0, view(Cp, msub, 1));
+    gemm64(c, kept, kept, m, 1.0, conj_of(trans(view(Oi, m, 1))), view(Cp, msub, 1), 0.0,
+           view(Hp, kept, 1));
+    jacobi_eigh(s, Hp, kept, wp, Yp, 60, jinfo);
+    const int kk = std::min(k, kept);
+    // C = Oi Yp[:, :kk]  ([m][kk], ld msub)
+    gemm64(c, m, kk, kept, 1.0, view(Oi, m, 1), view(Yp, kept, 1), 0.0, view(C, msub, 1));
+    CVS_CUDA(cudaMemcpyAsync(w.data(), wp, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+    // Ritz singles X1 = C^T V, S C = C^T (MV + R), residuals
+    gemm64(c, kk, (int)N1, m, 1.0, trans(view(C, msub, 1)), view(V, N1, 1), 0.0, view(T2, N1, 1));
+    gemm64(c, kk, (int)N1, m, 1.0, trans(view(C, msub, 1)), view(MV, N1, 1), 0.0, view(T, N1, 1));
+    gemm64(c, kk, (int)N1, m, 1.0, trans(view(C, msub, 1)), view(Rf, N1, 1), 1.0, view(T, N1, 1));
+    lift_coef(s, C, m, kk, msub, wp, thd, Cp);
+    // r1 = SC - w X1 (into T), the folded residual r~ = r1 - Cp^T D (into T + k N1)
+    row_axpy(s, T, T2, wp, kk, N1, T);
+    cplx* Rt = T + (int64_t)k * N1;
+    CVS_CUDA(cudaMemcpyAsync(Rt, T, (size_t)kk * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    gemm64(c, kk, (int)N1, m, -1.0, trans(view(Cp, msub, 1)), view(Df, N1, 1), 1.0, view(Rt, N1, 1));
+    row_norm2(s, T, kk, N1, rn1);
+    row_norm2(s, Rt, kk, N1, rnt);
+    // ||r2||^2 = Cp^H Q Cp (diagonal): G = Q Cp, then Cp^H G
+    gemm64(c, m, kk, m, 1.0, view(Q, msub, 1), view(Cp, msub, 1), 0.0, view(Hp, msub, 1));
+    gemm64(c, kk, kk, m, 1.0, conj_of(trans(view(Cp, msub, 1))), view(Hp, msub, 1), 0.0,
+           view(Yp, kk, 1));
+    CVS_CUDA(cudaMemcpyAsync(r1.data(), rn1, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemcpyAsync(rt.data(), rnt, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemcpyAsync(g2.data(), Yp, (size_t)kk * kk * sizeof(cplx), cudaMemcpyDeviceToHost, s));
+    c->sync();
+    res.iters = it + 1;
+    std::vector<double> rn(kk), rtn(kk);
+    std::vector<int> todo;
+    res.maxres = 0.0;
+    res.converged = 0;
+    for (int q = 0; q < kk; ++q) {
+      rn[q] = std::sqrt(std::max(0.0, r1[q] + std::max(0.0, g2[(size_t)q * kk + q].x)));
+      rtn[q] = std::sqrt(std::max(0.0, rt[q]));
+      res.maxres = std::max(res.maxres, rn[q]);
+      if (rn[q] <= tol) ++res.converged; else todo.push_back(q);
+    }
+    if (verbose())
+      fprintf(stderr, "[cvsadc] folded it %3d m %3d w0 %.12f max|r| %.3e folds %d\n", it, m,
+              w[0], res.maxres, res.folds);
+    if (todo.empty() || it == max_iter - 1) break;
+    if (stop_on_stagnation) {
+      hist.push_back(res.maxres);
+      if (hist.size() > 4 && res.maxres > 0.5 * hist[hist.size() - 5]) break;
+    }
+    bool stale = false;
+    for (int q : todo) stale = stale || rtn[q] < 0.5 * rn[q];
+    if (stale || m + (int)todo.size() > msub) {
+      // the Ritz singles, re-lifted at their Ritz values
+      CVS_CUDA(cudaMemcpyAsync(T, T2, (size_t)kk * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+      restart(T, w.data(), kk);
+      hist.clear();
+      continue;
+    }
+    // preconditioned folded residuals of the unconverged roots
+    const int cnt = (int)todo.size();
+    for (int q = 0; q < cnt; ++q)
+      if (todo[q] != q)
+        CVS_CUDA(cudaMemcpyAsync(Rt + (int64_t)q * N1, Rt + (int64_t)todo[q] * N1,
+                                 N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    std::vector<double> wt(cnt);
+    for (int q = 0; q < cnt; ++q) wt[q] = w[todo[q]];
+    if (c->sch_on) {
+      // t = U (w - lam)^-1 U^H r~   (S(theta0) = U diag(lam) U^H)
+      cplx* Ty = c->sch_tmp.c();
+      CVS_CUDA(cudaMemcpyAsync(rn1, wt.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+      gemm64(c, (int)N1, cnt, (int)N1, 1.0, conj_of(trans(view(c->sch_U.c(), N1, 1))),
+             view(Rt, 1, N1), 0.0, view(Ty, cnt, 1));
+      eig_shift(s, Ty, N1, cnt, c->sch_lam.d(), rn1);
+      gemm64(c, (int)N1, cnt, (int)N1, 1.0, view(c->sch_U.c(), N1, 1), view(Ty, cnt, 1), 0.0,
+             view(T, 1, N1));
+    } else {
+      CVS_CUDA(cudaMemcpyAsync(T, Rt, (size_t)cnt * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    }
+    const int m0 = m;
+    const int added = orth_append(T, cnt, true);
+    if (added == 0) break;
+    // each new direction is lifted at the Ritz value of the root whose
+    // correction it was started from (the block Gram-Schmidt is triangular)
+    for (int q = 0; q < added; ++q) th[m0 + q] = wt[std::min(std::max(src_h[q], 0), cnt - 1)];
+    m += added;
+    lift(m0, added);
+  }
+  CVS_CUDA(cudaMemcpyAsync(X1out, T2, (size_t)std::min(k, m) * N1 * sizeof(cplx),
+                           cudaMemcpyDeviceToDevice, s));
+  for (int q = 0; q < k; ++q) wout[q] = w[std::min(q, (int)w.size() - 1)];
+  c->sync();
+  return res;
+}
+
+// Oscillator strengths f_n = 2/3 w_n sum_x |X_n^H F^x|^2 (section
+// "Properties in ISR formulation") of nvec full vectors X [nvec][N] into f.
+void osc_strengths(cvsadc_ctx* c, const cplx* X, int nvec, const double* w, double* f) {
+  c->fd_th.ensure((size_t)(nvec * 3 * TS_CHUNKS + nvec * 3 + 8) * sizeof(cplx));
+  cplx* part = (cplx*)c->fd_th.p;
+  cplx* Tn = part + (size_t)nvec * 3 * TS_CHUNKS;
+  ts_dot(c->stream, X, nvec, c->F.c(), 3, c->N, part, Tn, 3, true);
+  std::vector<cplx> T((size_t)nvec * 3);
+  CVS_CUDA(cudaMemcpyAsync(T.data(), Tn, T.size() * sizeof(cplx), cudaMemcpyDeviceToHost,
+                           c->stream));
+  c->sync();
+  for (int r0 = 0; r0 < nvec; ++r0) {
+    double s2 = 0;
+    for (int x = 0; x < 3; ++x) {
+      const cplx t = T[(size_t)r0 * 3 + x];
+      s2 += t.x * t.x + t.y * t.y;
+    }
+    f[r0] = 2.0 / 3.0 * w[r0] * s2;
+  }
+}
+
+// Would the full-space Davidson (V, W [msub][N], X, AX [nkeep][N], T [k][N])
+// plus a sigma group fit in 85 % of the free device memory?
+bool full_space_fits(cvsadc_ctx* c, int k, int max_sub) {
+  const int msub = std::max(max_sub, 2 * k + 2);
+  const int nkeep = std::max(k, std::min(msub / 3, msub - 2 * k));
+  const double vec = (double)c->N * sizeof(cplx);
+  const double need = vec * (2.0 * msub + 2.0 * nkeep + k + 2.0 * 3 * k) +
+                      4.0 * (double)c->N1 * c->nval * c->nvirt * sizeof(cplx);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return true;
+  }
+  return need + (double)c->held_bytes() * 0.0 < 0.85 * (double)free_b;
+}
+
+// The doubles-folded solver behind cvsadc_davidson: roots, and (when asked)
+// the full eigenvectors (x1, W(w) M21 x1) normalised, and oscillator
+// strengths.
+void folded_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega, void* X,
+                  double* osc, cvsadc_info* info, double tol, int max_iter, int max_sub) {
+  const int k = p->nroots;
+  const int64_t N1 = c->N1, N = c->N;
+  cudaStream_t s = c->stream;
+  CVS_REQUIRE(k <= N1, CVSADC_EINVAL, "the folded solver finds at most N1 roots");
+  const bool dev = (p->flags & CVSADC_FLAG_DEVICE_PTRS) != 0;
+  const double t0 = now_ms();
+  c->sch_ms = 0.0;
+  c->sch_builds = 0;
+  c->sch_couplings = 0;
+  const bool use_schur = (p->flags & CVSADC_FLAG_DIAG_PRECOND) == 0;
+  if (!(use_schur && schur_setup(c))) c->sch_on = false;
+  const int prec = p->precision;
+  const bool refine = needs_refine(prec) && (p->flags & CVSADC_FLAG_NO_REFINE) == 0;
+  const double tol_phase = refine ? std::max(tol, mixed_tolerance(prec)) : tol;
+  DBuf X1, x0;
+  X1.ensure((size_t)k * N1 * sizeof(cplx));
+  std::vector<double> w(k), th0;
+  const cplx* start = nullptr;
+  int nstart = 0;
+  if (!c->sch_on) {
+    // no Schur eigenvectors: unit vectors at the smallest diagonal entries
+    // of M11, lifted 1 Eh (or 3 %) below the lowest M22 entry
+    nstart = (int)std::min<int64_t>(2 * k, N1);
+    c->dv_misc.ensure((size_t)(64 * 320 + 2048) * sizeof(double));
+    double* dwork = c->dv_misc.d();
+    int64_t* idx = (int64_t*)(dwork + 1024);
+    k_smallest(s, c->diag.d(), N1, nstart, idx, dwork);
+    std::vector<int64_t> hidx(nstart);
+    CVS_CUDA(cudaMemcpyAsync(hidx.data(), idx, nstart * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    x0.ensure((size_t)nstart * N1 * sizeof(cplx));
+    CVS_CUDA(cudaMemsetAsync(x0.p, 0, (size_t)nstart * N1 * sizeof(cplx), s));
+    c->sync();
+    const cplx one = cmake(1, 0);
+    for (int q = 0; q < nstart; ++q)
+      CVS_CUDA(cudaMemcpyAsync(x0.c() + (int64_t)q * N1 + hidx[q], &one, sizeof(cplx),
+                               cudaMemcpyHostToDevice, s));
+    std::vector<double> eps(c->n);
+    CVS_CUDA(cudaMemcpyAsync(eps.data(), c->eps.p, c->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    c->sync();
+    std::vector<double> ev(eps.begin() + c->o, eps.end());
+    std::sort(ev.begin(), ev.end());
+    const double pole = ev[0] + ev[1] - *std::max_element(eps.begin(), eps.begin() + c->ncore) -
+                        *std::max_element(eps.begin() + c->ncore, eps.begin() + c->o);
+    th0.assign(nstart, pole - std::max(1.0, 0.03 * std::fabs(pole)));
+    start = x0.c();
+  }
+  FoldResult r = folded_davidson(c, prec, k, max_iter, max_sub, tol_phase, start,
+                                 th0.empty() ? nullptr : th0.data(), nstart, X1.c(), w.data(),
+                                 refine, true);
+  const double t1 = now_ms();
+  double t_ref = 0.0;
+  if (refine) {
+    // FP64-class continuation from the converged Ritz singles, lifted at
+    // their roots
+    DBuf xs;
+    xs.ensure((size_t)k * N1 * sizeof(cplx));
+    CVS_CUDA(cudaMemcpyAsync(xs.p, X1.p, (size_t)k * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    std::vector<double> wr = w;
+    const int sweeps = p->refine_sweeps > 0 ? p->refine_sweeps : 20;
+    FoldResult r2 = folded_davidson(c, refine_precision(prec), k, sweeps, max_sub, tol, xs.c(),
+                                    wr.data(), k, X1.c(), w.data(), false, false);
+    r.iters += r2.iters;
+    r.folds += r2.folds;
+    r.converged = r2.converged;
+    r.maxres = r2.maxres;
+    t_ref = now_ms() - t1;
+  }
+  // full vectors when asked for: z = (x1, W(w) M21 x1) / ||.||, in groups
+  std::vector<double> f(k, 0.0);
+  const bool want_x = X && (p->flags & CVSADC_FLAG_RETURN_X);
+  const bool want_f = osc && c->has_dip;
+  if (want_x || want_f) {
+    const double per = 2.0 * (double)N * sizeof(cplx);
+    const int g = (int)std::max(1.0, std::min((double)k, 24e9 / per));
+    DBuf Z, Sg, th, nr;
+    Z.ensure((size_t)g * N * sizeof(cplx));
+    Sg.ensure((size_t)g * N * sizeof(cplx));
+    th.ensure((size_t)(g + 8) * sizeof(double));
+    nr.ensure((size_t)(g + 8) * sizeof(double));
+    for (int q0 = 0; q0 < k; q0 += g) {
+      const int gg = std::min(g, k - q0);
+      CVS_CUDA(cudaMemsetAsync(Z.p, 0, (size_t)gg * N * sizeof(cplx), s));
+      copyv(c, gg, (int)N1, 1.0, view(X1.c() + (int64_t)q0 * N1, N1, 1), view(Z.p, N, 1));
+      sigma_impl(c, prec == CVSADC_FP64 || !tc_available() ? CVSADC_FP64 : CVSADC_FP64_SLICE7,
+                 Z.c(), Sg.c(), gg, SIG_FWD);
+      CVS_CUDA(cudaMemcpyAsync(th.p, w.data() + q0, gg * sizeof(double), cudaMemcpyHostToDevice, s));
+      // doubles of Z = W(w) M21 x1 (singles kept)
+      fold_doubles(s, Sg.c(), nullptr, th.d(), gg, N, N1, c->ncore, c->nval, c->nvirt,
+                   c->eps.d(), false, Z.c());
+      copyv(c, gg, (int)N1, 1.0, view(X1.c() + (int64_t)q0 * N1, N1, 1), view(Z.p, N, 1));
+      row_norm2(s, Z.c(), gg, N, nr.d());
+      std::vector<double> hn(gg);
+      CVS_CUDA(cudaMemcpyAsync(hn.data(), nr.p, gg * sizeof(double), cudaMemcpyDeviceToHost, s));
+      c->sync();
+      for (double& x : hn) x = x > 0 ? 1.0 / std::sqrt(x) : 1.0;
+      CVS_CUDA(cudaMemcpyAsync(nr.p, hn.data(), gg * sizeof(double), cudaMemcpyHostToDevice, s));
+      scale_vectors(s, Z.c(), nr.d(), gg, N);
+      c->dv_misc.ensure((size_t)(152 * gg * 4 + 64) * sizeof(cplx));
+      phase_fix(s, Z.c(), gg, N, c->dv_misc.d());
+      if (want_f) osc_strengths(c, Z.c(), gg, w.data() + q0, f.data() + q0);
+      if (want_x)
+        download(c, (cplx*)X + (int64_t)q0 * N, Z.p, (size_t)gg * N * sizeof(cplx), dev);
+      c->sync();
+    }
+  }
+  if (dev) {
+    CVS_CUDA(cudaMemcpyAsync(omega, w.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (want_f)
+      CVS_CUDA(cudaMemcpyAsync(osc, f.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+  } else {
+    std::memcpy(omega, w.data(), k * sizeof(double));
+    if (want_f) std::memcpy(osc, f.data(), k * sizeof(double));
+  }
+  c->sync();
+  if (info) {
+    info->iterations = r.iters;
+    info->sigma_vectors = 0;
+    info->converged = r.converged;
+    info->max_residual = r.maxres;
+    info->t_davidson_ms = t1 - t0 - c->sch_ms;
+    info->t_refine_ms = t_ref;
+    info->t_sigma_ms = 0.0;
+    info->emp2 = c->emp2;
+    info->nvirt_kept = c->nvirt;
+    info->t_schur_ms = c->sch_ms;
+    info->schur_theta = c->sch_on ? c->sch_theta : 0.0;
+    info->coupling_vectors = c->sch_couplings;
+    info->schur_builds = c->sch_builds;
+  }
+  if (r.converged < k) throw Error{CVSADC_ENOTCONV, "folded solver did not converge"};
+}
+
 void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
                     void* X, double* osc, cvsadc_info* info) {
   CVS_REQUIRE(c->prepared, CVSADC_ESTATE, "no prepared problem");
@@ -1561,6 +2080,10 @@ void davidson_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega,
   int max_iter = p->max_iter > 0 ? p->max_iter : 400;
   int max_sub = p->max_subspace > 0 ? p->max_subspace : std::max(8 * k, 48);
   max_sub = std::min(max_sub, 128);
+  if ((p->flags & CVSADC_FLAG_FOLDED) || !full_space_fits(c, k, max_sub)) {
+    folded_entry(c, p, omega, X, osc, info, tol, max_iter, max_sub);
+    return;
+  }
   double t0 = now_ms();
   DBuf Xd;
   Xd.ensure((size_t)k * c->N * sizeof(cplx));

@@ -1,0 +1,92 @@
+"""The doubles-folded solver (CVSADC_FLAG_FOLDED) against the oracle.
+
+M22 is diagonal, so the eigenvalues of M below the lowest M22 entry are the
+fixed points of the singles-space pseudo-eigenvalue problem S(w) x1 = w x1,
+S(w) = M11 + M12 (w - M22)^-1 M21 (Eqs. 11-12).  The folded solver never
+stores a doubles vector; its Rayleigh-Ritz step is nevertheless the one of
+M in the full space, so FP64 roots must match the oracle's exact
+eigenvalues to 1e-9 Eh (the FP64 path's bar) and the mixed precision
+(SLICE4 with the FP64-class continuation) to 1e-5 Eh (the mixed bar: its
+problem, t2 and M11, is built with 4-slice products, ~1e-8 Eh here),
+oscillator strengths to 1e-8 of the largest, and the rebuilt full
+eigenvectors must be eigenvectors of the oracle's explicit matrix.
+"""
+
+TOL = {"fp64": 1e-9, "slice4": 1e-5}
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import adc2
+from oracle import solve as osolve
+from synth import make_instance
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.mark.parametrize("prec,precond", [("fp64", "schur"), ("slice4", "schur"),
+                                          ("fp64", "diag")])
+def test_folded_roots_and_osc_match_oracle(prec, precond):
+    import paper_2604_27451_gb300 as pkg
+
+    nc, nw, nv, L, k = 3, 7, 37, 70, 4
+    inst = make_instance(nc, nw, nv, L, seed=2)
+    ref = osolve.solve(inst.eps, inst.B, inst.dip, nc, nw, nv, k, method="partitioned")
+    ctx = pkg.Context(0)
+    out = ctx.solve(inst.eps, inst.B, inst.dip, nc, nw, nv, k, precision=prec, conv=1e-8,
+                    precond=precond, solver="folded", return_x=True, max_iter=400)
+    assert out["status"] == 0, out["info"]
+    assert out["info"]["sigma_vectors"] == 0  # no full-space sigma was built
+    assert np.abs(out["omega"] - ref["omega"]).max() < TOL[prec]
+    assert np.abs(out["osc"] - ref["osc"]).max() < 1e-8 * np.abs(ref["osc"]).max()
+    # the rebuilt full vectors: normalised eigenvectors of the explicit M
+    M11 = adc2.m11(inst.eps, inst.B, nc, nw, nv)
+    sig = adc2.Sigma(inst.eps, inst.B, nc, nw, nv, M11=M11)
+    X = out["X"]
+    N1 = nc * nv
+    for q in range(k):
+        x = X[q]
+        s1, s2 = sig(x[:N1], x[N1:])
+        r = np.concatenate([s1, s2]) - out["omega"][q] * x
+        assert abs(np.linalg.norm(x) - 1.0) < 1e-10
+        assert np.linalg.norm(r) < (1e-7 if prec == "fp64" else 1e-5)
+    ctx.close()
+
+
+def test_folded_small_workload_golden():
+    """The small workload (6/14/40/240, 4 roots) against the stored exact
+    roots and oscillator strengths (tests/golden/small_fp64.json, written by
+    the oracle)."""
+    import paper_2604_27451_gb300 as pkg
+
+    g = json.load(open(os.path.join(GOLDEN, "small_fp64.json")))
+    sh = g["shape"]
+    inst = make_instance(sh["ncore"], sh["nval"], sh["nvirt"], sh["naux"], seed=g["seed"])
+    ctx = pkg.Context(0)
+    for prec in ("fp64", "slice4"):
+        out = ctx.solve(inst.eps, inst.B, inst.dip, sh["ncore"], sh["nval"], sh["nvirt"],
+                        sh["nroots"], precision=prec, conv=1e-8, solver="folded")
+        assert out["status"] == 0, (prec, out["info"])
+        assert np.abs(out["omega"] - np.array(g["omega"])).max() < TOL[prec], prec
+        assert np.abs(out["osc"] - np.array(g["osc"])).max() < 1e-6 * max(g["osc"]), prec
+    ctx.close()
+
+
+def test_folded_agrees_with_full_space_solver():
+    """Same roots from the two solvers on a problem with more roots (8)."""
+    import paper_2604_27451_gb300 as pkg
+
+    nc, nw, nv, L, k = 4, 10, 50, 150, 8
+    inst = make_instance(nc, nw, nv, L, seed=9)
+    ctx = pkg.Context(0)
+    a = ctx.solve(inst.eps, inst.B, None, nc, nw, nv, k, precision="fp64", conv=1e-8)
+    b = ctx.solve(inst.eps, inst.B, None, nc, nw, nv, k, precision="fp64", conv=1e-8,
+                  solver="folded")
+    assert a["status"] == 0 and b["status"] == 0
+    assert np.abs(a["omega"] - b["omega"]).max() < 1e-9
+    ctx.close()
