@@ -468,6 +468,26 @@ def extras(args, state, inst, stream, torch, pkg):
     res["time_to_roots_medium"] = ttm
     del e_, B_, d_, me
     torch.cuda.empty_cache()
+    if args.ttr_large:
+        # the large workload itself: the full-space subspace does not fit, so
+        # the doubles-folded solver runs (singles-space vectors only)
+        wl = WORKLOADS["large"]
+        e_ = torch.from_numpy(inst.eps).to(dev)
+        B_ = torch.from_numpy(inst.B).to(dev)
+        ttl = {"workload": "large CVS-ADC(2): ncore %d, nval %d, nvirt %d, naux %d, %d roots, "
+                           "residual 1e-6, inputs resident, no dipoles" % (
+                               wl["ncore"], wl["nval"], wl["nvirt"], wl["naux"], wl["nroots"])}
+        rl = {}
+        for p in args.ttr_large.split(","):
+            rl[p], ttl[p] = solve_entry(e_, B_, None, wl, p, conv=1e-6)
+        for p in rl:
+            if p != "slice4" and "slice4" in rl:
+                ttl["max_abs_root_diff_slice4_vs_%s_Eh" % p] = float(np.abs(rl["slice4"] - rl[p]).max())
+                ttl["speedup_slice4_vs_%s" % p] = round(ttl[p]["s"] / ttl["slice4"]["s"], 2)
+        ttl["roots_Eh"] = {p: [round(float(x), 9) for x in r] for p, r in rl.items()}
+        res["time_to_roots_large"] = ttl
+        del e_, B_
+        torch.cuda.empty_cache()
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds, rows=max(1, inst.nvirt // 8))
     return res
@@ -590,6 +610,9 @@ def main():
                     help="time K instances of the batched workload instead")
     ap.add_argument("--ttr-medium-fp64", action="store_true",
                     help="also time the FP64 solve of the medium workload (minutes)")
+    ap.add_argument("--ttr-large", default="",
+                    help="comma-separated precisions whose full solve of the large "
+                         "workload is timed (e.g. slice4,fp64_slice7)")
     ap.add_argument("--profile-gemm", action="store_true",
                     help="run one 4096^3 complex GEMM three times (ncu case)")
     args = ap.parse_args()

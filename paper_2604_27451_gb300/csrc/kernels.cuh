@@ -180,6 +180,8 @@ void jacobi_eigh(cudaStream_t s, cplx* A, int n, double* w, cplx* Vec,
 // Schur-complement preconditioner (schur_kernels.cu)
 void h_assemble(cudaStream_t s, const cplx* hc1, const cplx* hc2, int nc,
                 int nw, int nv, cplx* h);
+// G[jl][a][b][c] = <ab||cj> from X1 = (ac|bj) and X2 = (aj|bc); with X2 ==
+// NULL the second comes from X1 as (bc|aj)
 void g_assemble(cudaStream_t s, const cplx* X1, const cplx* X2, int jc, int nv,
                 cplx* G);
 void g_weight(cudaStream_t s, const cplx* G, int jc, int j0, int nc, int nw,
@@ -214,6 +216,14 @@ void row_axpy(cudaStream_t s, const cplx* X, const cplx* Z, const double* w, int
 void row_norm2(cudaStream_t s, const cplx* X, int k, int64_t n, double* out);
 void inv_sqrt_cols(cudaStream_t s, const cplx* U, const double* w, int m, int off, int kept,
                    int ldu, cplx* Oi);
+void h_weight_mean(cudaStream_t s, const cplx* h, int j, int nc, int nw, int nv,
+                   const double* eps, double theta, double ebar, int power, cplx* Hw);
+void add_row_scaled(cudaStream_t s, cplx* C, const cplx* P, int nv, int nq,
+                    const double* eps, int o, double ebar);
+void eig_shift_partial(cudaStream_t s, cplx* Y, int p, int k, const double* lam,
+                       const double* d, double theta0, const double* theta, double lam_c);
+void eig_shift_d(cudaStream_t s, cplx* Y, int64_t n1, int k, const double* lam,
+                 const double* d, double theta0, const double* theta);
 void add_singles(cudaStream_t s, const cplx* a, const cplx* b, int64_t N,
                  int64_t n1, int k, cplx* out);
 

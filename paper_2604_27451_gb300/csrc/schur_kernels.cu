@@ -85,7 +85,9 @@ __global__ void g_assemble_kernel(const cplx* __restrict__ X1,
     const int a = r % v;
     const int jl = r / v;
     const cplx x1 = X1[((int64_t)a * v + c) * (jc * v) + (int64_t)jl * v + b];
-    const cplx x2 = X2[((int64_t)jl * v + a) * (v * v) + (int64_t)b * v + c];
+    // (aj|bc) = (bc|aj): without X2 it is the permuted element of X1
+    const cplx x2 = X2 ? X2[((int64_t)jl * v + a) * (v * v) + (int64_t)b * v + c]
+                       : X1[((int64_t)b * v + c) * (jc * v) + (int64_t)jl * v + a];
     G[e] = csub(x1, x2);
   }
 }
@@ -156,6 +158,60 @@ __global__ void h_weight_kernel(const cplx* __restrict__ h, int j, int nc,
     const int cp = r / nv;
     const cplx x = h[(((int64_t)Kp * nv + b) * nc + K) * nw + j];
     Hw[e] = cscale(x, wgt(eps, nc, o, theta, K, j, cp, b));
+  }
+}
+
+// Hw[b][(K,K')] = wbar^p h[K'][b][K][j] with the weight taken at the mean
+// virtual energy ebar in place of e_c' (p = 1, 2): the large-singles-space
+// preconditioner's cross term (12), w(e_c') = wbar + (e_c' - ebar) wbar^2
+// + O((e_c' - ebar)^2 wbar^3)
+__global__ void h_weight_mean_kernel(const cplx* __restrict__ h, int j, int nc, int nw,
+                                     int nv, const double* __restrict__ eps, double theta,
+                                     double ebar, int power, cplx* __restrict__ Hw) {
+  const int o = nc + nw;
+  const int64_t total = (int64_t)nv * nc * nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int Kp = e % nc;
+    int64_t r = e / nc;
+    const int K = r % nc;
+    const int b = r / nc;
+    const double w = 1.0 / (theta - (ebar + eps[o + b] - eps[K] - eps[nc + j]));
+    const cplx x = h[(((int64_t)Kp * nv + b) * nc + K) * nw + j];
+    Hw[e] = cscale(x, power == 2 ? w * w : w);
+  }
+}
+
+// C[(c', c)][q] += (e_c' - ebar) P[(c', c)][q] over q < nq
+__global__ void add_row_scaled_kernel(cplx* __restrict__ C, const cplx* __restrict__ P,
+                                      int nv, int nq, const double* __restrict__ eps,
+                                      int o, double ebar) {
+  const int64_t total = (int64_t)nv * nv * nq;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int cp = (int)(e / ((int64_t)nv * nq));
+    C[e] = cadd(C[e], cscale(P[e], eps[o + cp] - ebar));
+  }
+}
+
+// Partial eigensystem preconditioner: Y[i][r] (i < p, U_p^H r~) becomes
+// Y (1/den_i(r) - 1/(theta_r - lam_c)) with den_i = theta_r - lam_i +
+// (theta_r - theta0) d_i, so that U_p Y + r~ / (theta_r - lam_c) applies
+// (S - theta)^-1 on the computed eigenvectors and a scalar on the rest.
+__global__ void eig_shift_partial_kernel(cplx* Y, int p, int k,
+                                         const double* __restrict__ lam,
+                                         const double* __restrict__ d, double theta0,
+                                         const double* __restrict__ theta, double lam_c) {
+  const int64_t total = (int64_t)p * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = e % k;
+    const int64_t i = e / k;
+    double den = theta[r] - lam[i] + (theta[r] - theta0) * d[i];
+    if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+    double dc = theta[r] - lam_c;
+    if (fabs(dc) < 1e-8) dc = dc < 0 ? -1e-8 : 1e-8;
+    Y[e] = cscale(Y[e], 1.0 / den - 1.0 / dc);
   }
 }
 
@@ -420,6 +476,24 @@ __global__ void eig_shift_kernel(cplx* Y, int64_t n1, int k,
   }
 }
 
+// Y[i][r] /= (theta_r - lam_i(theta_r)) with the eigenvalues of S(theta)
+// taken to first order about theta0: lam_i(theta) ~ lam_i - (theta -
+// theta0) d_i, d_i = u_i^H M12 W(theta0)^2 M21 u_i (Y is [n1][k])
+__global__ void eig_shift_d_kernel(cplx* Y, int64_t n1, int k,
+                                   const double* __restrict__ lam,
+                                   const double* __restrict__ d, double theta0,
+                                   const double* __restrict__ theta) {
+  const int64_t total = n1 * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = e % k;
+    const int64_t i = e / k;
+    double den = theta[r] - lam[i] + (theta[r] - theta0) * d[i];
+    if (fabs(den) < 1e-8) den = den < 0 ? -1e-8 : 1e-8;
+    Y[e] = cscale(Y[e], 1.0 / den);
+  }
+}
+
 // out[r][s] = a[r][s] + b[r][s] over the first n1 entries of k vectors of
 // length N
 __global__ void add_singles_kernel(const cplx* __restrict__ a,
@@ -673,6 +747,33 @@ void diag_precond(cudaStream_t s, const cplx* r, double theta,
 void eig_shift(cudaStream_t s, cplx* Y, int64_t n1, int k, const double* lam,
                const double* theta) {
   eig_shift_kernel<<<grid1d(n1 * k, 256), 256, 0, s>>>(Y, n1, k, lam, theta);
+  CVS_CHECK_LAUNCH();
+}
+
+void h_weight_mean(cudaStream_t s, const cplx* h, int j, int nc, int nw, int nv,
+                   const double* eps, double theta, double ebar, int power, cplx* Hw) {
+  h_weight_mean_kernel<<<grid1d((int64_t)nv * nc * nc, 256), 256, 0, s>>>(
+      h, j, nc, nw, nv, eps, theta, ebar, power, Hw);
+  CVS_CHECK_LAUNCH();
+}
+
+void add_row_scaled(cudaStream_t s, cplx* C, const cplx* P, int nv, int nq,
+                    const double* eps, int o, double ebar) {
+  add_row_scaled_kernel<<<grid1d((int64_t)nv * nv * nq, 256), 256, 0, s>>>(C, P, nv, nq, eps,
+                                                                          o, ebar);
+  CVS_CHECK_LAUNCH();
+}
+
+void eig_shift_partial(cudaStream_t s, cplx* Y, int p, int k, const double* lam,
+                       const double* d, double theta0, const double* theta, double lam_c) {
+  eig_shift_partial_kernel<<<grid1d((int64_t)p * k, 256), 256, 0, s>>>(Y, p, k, lam, d, theta0,
+                                                                       theta, lam_c);
+  CVS_CHECK_LAUNCH();
+}
+
+void eig_shift_d(cudaStream_t s, cplx* Y, int64_t n1, int k, const double* lam,
+                 const double* d, double theta0, const double* theta) {
+  eig_shift_d_kernel<<<grid1d(n1 * k, 256), 256, 0, s>>>(Y, n1, k, lam, d, theta0, theta);
   CVS_CHECK_LAUNCH();
 }
 

@@ -175,6 +175,12 @@ struct cvsadc_ctx {
   DBuf sch_W, sch_g, sch_S, sch_U, sch_V, sch_lam, sch_C11, sch_C12, sch_work,
       sch_tmp, sch_th;
   bool sch_on = false;
+  // eigenvectors held in sch_U ([N1][sch_p] columns): all N1, or the lowest
+  // SCHUR_PL for large singles spaces (the folded solver only)
+  int sch_p = 0;
+  // first-order drift of the Schur eigenvalues with theta (folded solver)
+  DBuf sch_d;
+  bool sch_d_on = false;
   double sch_theta = 0.0, sch_ms = 0.0, sch_pole = 0.0;
   int sch_builds = 0, sch_couplings = 0;
 
@@ -875,10 +881,9 @@ int schur_precision() {
   return tc_available() ? CVSADC_MIXED_SLICE4 : CVSADC_FP64;
 }
 
-// <ab||cj> for j in [j0, j0 + jc) into G[jl][a][b][c]; X1, X2 hold
-// jc v^3 complex each
-void build_g_chunk(cvsadc_ctx* c, int prec, int j0, int jc, cplx* X1, cplx* X2,
-                   cplx* G) {
+// <ab||cj> for j in [j0, j0 + jc) into G[jl][a][b][c]; X1 holds jc v^3
+// complex.  One GEMM: (aj|bc) = (bc|aj) is an element of the same product.
+void build_g_chunk(cvsadc_ctx* c, int prec, int j0, int jc, cplx* X1, cplx* G) {
   const int nc = c->ncore, v = c->nvirt, o = c->o, n = c->n, L = c->naux;
   const int64_t nn = (int64_t)n * n;
   const cplx* B = c->B.c();
@@ -887,35 +892,46 @@ void build_g_chunk(cvsadc_ctx* c, int prec, int j0, int jc, cplx* X1, cplx* X2,
        rows2(view(B + (int64_t)o * n + o, 0, nn), n, 1, v),
        cols2(view(B + (int64_t)o * n + nc + j0, nn, 0), 1, n, v), 0.0,
        view(X1, (int64_t)jc * v, 1));
-  // X2[(jl,a)][(b,c)] = sum_P B^P_aj B^P_bc
-  gemm(c, prec, jc * v, v * v, L, 1.0,
-       rows2(view(B + (int64_t)o * n + nc + j0, 0, nn), 1, n, v),
-       cols2(view(B + (int64_t)o * n + o, nn, 0), n, 1, v), 0.0,
-       view(X2, (int64_t)v * v, 1));
-  g_assemble(c->stream, X1, X2, jc, v, G);
+  g_assemble(c->stream, X1, nullptr, jc, v, G);
 }
 
-// j per chunk so that the chunk buffers (X1, X2, G and ncore weighted
-// copies) stay within ~6 GB
+// j per chunk so that the chunk buffers (X1, G and ncore weighted copies)
+// stay within ~6 GB
 int schur_jchunk(cvsadc_ctx* c) {
-  const double per_j = (3.0 + c->ncore) * std::pow((double)c->nvirt, 3) * sizeof(cplx);
+  const double per_j = (2.0 + c->ncore) * std::pow((double)c->nvirt, 3) * sizeof(cplx);
   return (int)std::max(1.0, std::min((double)c->nval, 6e9 / per_j));
 }
 
-// S(theta) into sch_S (schur_eigh decomposes it)
-void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached) {
-  const int nc = c->ncore, nw = c->nval, v = c->nvirt;
+// singles spaces above this size take the large-space preconditioner: the
+// lowest SCHUR_PL eigenpairs of S(theta0) from a block Davidson instead of
+// a full decomposition, and the cross term (12) with the weight expanded
+// to first order about the mean virtual energy
+constexpr int64_t SCHUR_FULL_MAX = 4096;
+constexpr int SCHUR_PL = 64;
+
+// S(theta) into sch_S (schur_eigh decomposes it).  approx12: the (12)
+// cross term with the weight w(e_c') expanded to first order about the mean
+// virtual energy, as two GEMMs per valence spinor (preconditioner use for
+// large singles spaces; the exact term is a batched product per c')
+void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached, bool approx12 = false) {
+  const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o;
   const int64_t v3 = (int64_t)v * v * v;
   cudaStream_t s = c->stream;
   const int jc = schur_jchunk(c);
   CVS_CUDA(cudaMemsetAsync(c->sch_C11.p, 0, (size_t)nc * v * v * sizeof(cplx), s));
   CVS_CUDA(cudaMemsetAsync(c->sch_C12.p, 0,
                            (size_t)v * v * nc * nc * sizeof(cplx), s));
-  // chunk buffers: [X1 | X2 | G | Gw (ncore copies)] (X1, X2, G unused when
-  // cached)
+  double ebar = 0.0;
+  if (approx12) {
+    std::vector<double> ev(v);
+    CVS_CUDA(cudaMemcpyAsync(ev.data(), c->eps.d() + o, v * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    c->sync();
+    for (double x : ev) ebar += x / v;
+  }
+  // chunk buffers: [X1 | G | Gw (ncore copies)] (X1, G unused when cached)
   cplx* X1 = c->sch_work.c();
-  cplx* X2 = X1 + (int64_t)jc * v3;
-  cplx* Gt = X2 + (int64_t)jc * v3;
+  cplx* Gt = X1 + (int64_t)jc * v3;
   cplx* Gw = Gt + (int64_t)jc * v3;
   cplx* Hw = c->sch_tmp.c();
   const bool vb = verbose();
@@ -926,7 +942,7 @@ void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached) {
     if (cached)
       G = c->sch_g.c() + (int64_t)j0 * v3;
     else
-      build_g_chunk(c, prec, j0, jn, X1, X2, Gt);
+      build_g_chunk(c, prec, j0, jn, X1, Gt);
     // (11): C11[(K,c)][c'] += sum_{jab} 1/2 w_Kjab conj(g_abc) g_abc', all K
     // in one GEMM (rows (K, c) of the weighted copies)
     g_weight(s, G, jn, j0, nc, nw, v, c->eps.d(), theta, Gw);
@@ -940,6 +956,18 @@ void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached) {
     }
     // (12): C12[c'][c][K][K'] += sum_b conj(<c'b||cj>) w_{Kjc'b} <K'b||Kj>
     for (int jl = 0; jl < jn; ++jl) {
+      if (approx12) {
+        // w = wbar + (e_c' - ebar) wbar^2: rows (c', c), columns (K, K')
+        const View Gc = conj_of(rows2(view(G + (int64_t)jl * v3, 0, v), (int64_t)v * v, 1, v));
+        h_weight_mean(s, c->h1.c(), j0 + jl, nc, nw, v, c->eps.d(), theta, ebar, 1, Hw);
+        gemm(c, prec, v * v, nc * nc, v, 1.0, Gc, view(Hw, nc * nc, 1), 1.0,
+             view(c->sch_C12.c(), nc * nc, 1));
+        h_weight_mean(s, c->h1.c(), j0 + jl, nc, nw, v, c->eps.d(), theta, ebar, 2, Hw);
+        gemm(c, prec, v * v, nc * nc, v, 1.0, Gc, view(Hw, nc * nc, 1), 0.0,
+             view(c->sch_V.c(), nc * nc, 1));
+        add_row_scaled(s, c->sch_C12.c(), c->sch_V.c(), v, nc * nc, c->eps.d(), o, ebar);
+        continue;
+      }
       h_weight(s, c->h1.c(), j0 + jl, nc, nw, v, c->eps.d(), theta, Hw);
       gemm(c, CVSADC_FP64, v, nc * nc, v, 1.0,
            batched(conj_of(view(G + (int64_t)jl * v3, 1, v)), (int64_t)v * v),
@@ -966,6 +994,138 @@ void build_schur(cvsadc_ctx* c, int prec, double theta, bool cached) {
 size_t schur_th_doubles(int64_t N1) {
   const size_t cc_n = (size_t)(N1 / 2 + 2);
   return 736 + ((cc_n + 1) & ~(size_t)1) + 2 * cc_n;
+}
+
+// Lowest p eigenpairs of the dense Hermitian sch_S (N1 x N1) into sch_U
+// ([N1][p], columns) and sch_lam, by block Davidson with S products as FP64
+// GEMMs, the diagonal preconditioner, FP64 subspace algebra and the Jacobi
+// kernel for the small projected matrices.  Residuals to 1e-6 of the
+// spectral scale: this is the preconditioner's eigensystem.
+__global__ void diag_real_kernel(const cplx* __restrict__ S, int64_t n, double* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = S[i * n + i].x;
+}
+
+void schur_eigh_partial(cvsadc_ctx* c, int p) {
+  const double t0 = verbose() ? (c->sync(), now_ms()) : 0.0;
+  const int64_t n = c->N1;
+  cudaStream_t s = c->stream;
+  const int ms = std::min<int64_t>(3 * p, n);
+  DBuf Xb, AXb, Tb, U, AU, sm, dS, rpart;
+  rpart.ensure((size_t)(304 * p + 64) * sizeof(double));
+  Xb.ensure((size_t)ms * n * sizeof(cplx));
+  AXb.ensure((size_t)ms * n * sizeof(cplx));
+  Tb.ensure((size_t)p * n * sizeof(cplx));
+  U.ensure((size_t)p * n * sizeof(cplx));
+  AU.ensure((size_t)p * n * sizeof(cplx));
+  const size_t TSP = (size_t)96 * 192 * TS_CHUNKS;
+  sm.ensure(((size_t)4 * ms * ms + 64 * 64 * 2 + TSP) * sizeof(cplx) +
+            (size_t)(4 * ms + 4096) * sizeof(double));
+  dS.ensure((size_t)n * sizeof(double));
+  cplx* H = sm.c();
+  cplx* A = H + (size_t)ms * ms;
+  cplx* Y = A + (size_t)ms * ms;
+  cplx* Cp = Y + (size_t)ms * ms;
+  cplx* G0 = Cp + (size_t)ms * ms;
+  cplx* Xo = G0 + 64 * 64;
+  cplx* tsp = Xo + 64 * 64;
+  double* w = (double*)(tsp + TSP);
+  double* rn = w + ms;
+  double* dw = rn + ms;
+  double* nrm0 = dw + 2 * ms;
+  int* kept_d = (int*)(nrm0 + 256);
+  diag_real_kernel<<<grid1d(n, 256), 256, 0, s>>>(c->sch_S.c(), n, dS.d());
+  CVS_CHECK_LAUNCH();
+  cplx* X = Xb.c();
+  cplx* AX = AXb.c();
+  int m = 0;
+  auto append = [&](cplx* T, int cnt) {
+    int added = 0;
+    for (int q0 = 0; q0 < cnt && m < ms; q0 += 64) {
+      const int cn = std::min(64, cnt - q0);
+      cplx* Tq = T + (int64_t)q0 * n;
+      ts_dot(s, Tq, cn, Tq, cn, n, tsp, G0, cn, true);
+      gram_diag_sqrt(s, G0, cn, cn, nrm0);
+      for (int pass = 0; pass < 2 && m > 0; ++pass) {
+        ts_dot(s, X, m, Tq, cn, n, tsp, Cp, cn, true);
+        ts_subtract(s, X, m, Cp, cn, cn, n, Tq, true);
+      }
+      ts_dot(s, Tq, cn, Tq, cn, n, tsp, G0, cn, true);
+      block_orth(s, G0, cn, cn, nrm0, 1e-10, Xo, kept_d);
+      int kept = 0;
+      CVS_CUDA(cudaMemcpyAsync(&kept, kept_d, sizeof(int), cudaMemcpyDeviceToHost, s));
+      c->sync();
+      kept = std::min(kept, ms - m);
+      if (kept <= 0) continue;
+      ts_combine(s, Tq, Xo, nullptr, nullptr, cn, cn, kept, n, X + (int64_t)m * n, true);
+      // S x for the new rows: (S x)^T = x^T S^T
+      gemm64(c, kept, (int)n, (int)n, 1.0, view(X + (int64_t)m * n, n, 1),
+             trans(view(c->sch_S.c(), n, 1)), 0.0, view(AX + (int64_t)m * n, n, 1));
+      m += kept;
+      added += kept;
+    }
+    return added;
+  };
+  // start: unit vectors at the p smallest diagonal entries
+  {
+    int64_t* idx = (int64_t*)(dw);
+    DBuf kw;
+    kw.ensure(4096 * sizeof(double));
+    const int kk = std::min(p, 64);
+    k_smallest(s, dS.d(), n, kk, (int64_t*)(nrm0 + 512), kw.d());
+    std::vector<int64_t> hi(kk);
+    CVS_CUDA(cudaMemcpyAsync(hi.data(), nrm0 + 512, kk * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemsetAsync(Tb.p, 0, (size_t)kk * n * sizeof(cplx), s));
+    c->sync();
+    const cplx one = cmake(1, 0);
+    for (int q = 0; q < kk; ++q)
+      CVS_CUDA(cudaMemcpyAsync(Tb.c() + q * n + hi[q], &one, sizeof(cplx), cudaMemcpyHostToDevice, s));
+    (void)idx;
+    append(Tb.c(), kk);
+  }
+  double scale = 1.0;
+  int it = 0;
+  std::vector<double> hw(ms), hr(p);
+  for (; it < 300; ++it) {
+    ts_dot(s, X, m, AX, m, n, tsp, H, m, true);
+    hermitize(s, H, m, m, A, m);
+    jacobi_eigh(s, A, m, w, Y, 60, dw);
+    const int kk = std::min(p, m);
+    // Ritz vectors U = Y[:, :kk]^T X, AU = Y^T AX
+    ts_combine(s, X, Y, nullptr, nullptr, m, m, kk, n, U.c(), true);
+    ts_combine(s, nullptr, nullptr, AX, Y, m, m, kk, n, AU.c(), true);
+    residual_precond(s, AU.c(), U.c(), w, dS.d(), kk, n, Tb.c(), rpart.d(), rn);
+    CVS_CUDA(cudaMemcpyAsync(hw.data(), w, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CVS_CUDA(cudaMemcpyAsync(hr.data(), rn, kk * sizeof(double), cudaMemcpyDeviceToHost, s));
+    c->sync();
+    scale = std::max(std::fabs(hw[0]), std::fabs(hw[m - 1]));
+    std::vector<int> todo;
+    for (int q = 0; q < kk; ++q)
+      if (std::sqrt(std::max(hr[q], 0.0)) > 1e-6 * scale) todo.push_back(q);
+    if (todo.empty() || kk < p) {
+      if (todo.empty()) break;
+    }
+    if (m + (int)todo.size() > ms) {
+      CVS_CUDA(cudaMemcpyAsync(X, U.p, (size_t)kk * n * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+      CVS_CUDA(cudaMemcpyAsync(AX, AU.p, (size_t)kk * n * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+      m = kk;
+    }
+    for (size_t q = 0; q < todo.size(); ++q)
+      if (todo[q] != (int)q)
+        CVS_CUDA(cudaMemcpyAsync(Tb.c() + q * n, Tb.c() + (int64_t)todo[q] * n,
+                                 n * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
+    if (append(Tb.c(), (int)todo.size()) == 0) break;
+  }
+  // sch_U columns = U rows; eigenvalues ascending
+  copyv(c, p, (int)n, 1.0, view(U.p, n, 1), view(c->sch_U.p, 1, p));
+  CVS_CUDA(cudaMemcpyAsync(c->sch_lam.p, w, p * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  ++c->sch_builds;
+  if (verbose()) {
+    c->sync();
+    fprintf(stderr, "[cvsadc] schur partial eigh n %lld p %d: %d iterations, %.1f ms, lam0 %.6f\n",
+            (long long)n, p, it, now_ms() - t0, hw[0]);
+  }
 }
 
 // Eigen-decomposition of sch_S into sch_U / sch_lam.  With warm set,
@@ -1063,13 +1223,15 @@ void schur_init(cvsadc_ctx* c) {
   const int64_t N1 = c->N1;
   const int jc = schur_jchunk(c);
   const int64_t v3 = (int64_t)v * v * v;
+  const bool large = N1 > SCHUR_FULL_MAX;
+  c->sch_p = large ? (int)std::min<int64_t>(SCHUR_PL, N1) : (int)N1;
   c->sch_S.ensure((size_t)N1 * N1 * sizeof(cplx));
-  c->sch_U.ensure((size_t)N1 * N1 * sizeof(cplx));
+  c->sch_U.ensure((size_t)N1 * c->sch_p * sizeof(cplx));
   c->sch_V.ensure((size_t)N1 * N1 * sizeof(cplx));
   c->sch_lam.ensure((size_t)N1 * sizeof(double));
   c->sch_C11.ensure((size_t)nc * v * v * sizeof(cplx));
   c->sch_C12.ensure((size_t)v * v * nc * nc * sizeof(cplx));
-  c->sch_work.ensure((size_t)(3 + nc) * jc * v3 * sizeof(cplx));
+  c->sch_work.ensure((size_t)(2 + nc) * jc * v3 * sizeof(cplx));
   c->sch_tmp.ensure(std::max((size_t)v * v * nc * nc, (size_t)N1 * 64) * sizeof(cplx));
   c->sch_th.ensure(schur_th_doubles(N1) * sizeof(double) + 256);
 }
@@ -1080,6 +1242,9 @@ void schur_init(cvsadc_ctx* c) {
 // f(theta) = lam0(S(theta)) - theta, which is concave and decreasing below
 // the lowest M22 entry, started just below it: the iterates decrease
 // monotonically towards the lowest root and stay above it.
+void fold_apply(cvsadc_ctx* c, int prec, const cplx* V, int b, const double* th,
+                cplx* R, cplx* D);
+
 bool schur_setup(cvsadc_ctx* c) {
   const double t0 = now_ms();
   c->sch_on = false;
@@ -1087,8 +1252,11 @@ bool schur_setup(cvsadc_ctx* c) {
   c->sch_couplings = 0;
   const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n;
   const int64_t N1 = c->N1, N = c->N;
-  if (N1 > 4096 || v < 2) return false;
-  const int prec = schur_precision();
+  if (N1 > 3 * SCHUR_FULL_MAX || v < 2) return false;
+  // large singles spaces: BF16X3 products for the build (it only steers the
+  // iteration), the approximate cross term and the partial eigensystem
+  const bool large = N1 > SCHUR_FULL_MAX;
+  const int prec = large && tc_available() ? CVSADC_MIXED_BF16X3 : schur_precision();
   cudaStream_t s = c->stream;
   // lowest M22 entry
   std::vector<double> eps(n);
@@ -1112,11 +1280,61 @@ bool schur_setup(cvsadc_ctx* c) {
   if (gbytes <= std::min(0.3 * (double)free_b, 48e9)) {
     c->sch_g.ensure((size_t)gbytes);
     cplx* X1 = c->sch_work.c();
-    cplx* X2 = X1 + (int64_t)jc * v3;
     for (int j0 = 0; j0 < nw; j0 += jc)
-      build_g_chunk(c, prec, j0, std::min(jc, nw - j0), X1, X2,
+      build_g_chunk(c, prec, j0, std::min(jc, nw - j0), X1,
                     c->sch_g.c() + (int64_t)j0 * v3);
     cached = true;
+  }
+  if (large) {
+    // two builds: at the start point below the pole, then at the fixed point
+    // of the lowest eigenvector's lift, found by Newton steps on that lift
+    // (omega <- theta + (lam - theta) / (1 + ||W M21 u||^2), one fold each)
+    double theta = pole - std::max(1.0, 0.03 * std::fabs(pole));
+    DBuf u, R, D, MU, dots;
+    u.ensure((size_t)N1 * sizeof(cplx));
+    R.ensure((size_t)N1 * sizeof(cplx));
+    D.ensure((size_t)N1 * sizeof(cplx));
+    MU.ensure((size_t)N1 * sizeof(cplx));
+    dots.ensure((size_t)(8 + 3 * TS_CHUNKS) * sizeof(cplx));
+    for (int b = 0; b < 2; ++b) {
+      build_schur(c, prec, theta, cached, true);
+      schur_eigh_partial(c, c->sch_p);
+      double lam0 = 0.0;
+      CVS_CUDA(cudaMemcpyAsync(&lam0, c->sch_lam.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+      c->sync();
+      if (!std::isfinite(lam0) || (b == 0 && lam0 >= pole)) break;
+      c->sch_theta = theta;
+      c->sch_on = true;
+      if (b == 1) break;
+      copyv(c, 1, (int)N1, 1.0, view(c->sch_U.c(), 1, c->sch_p), view(u.p, N1, 1));
+      gemm64(c, 1, (int)N1, (int)N1, 1.0, view(u.p, N1, 1), trans(view(c->M11.c(), N1, 1)),
+             0.0, view(MU.p, N1, 1));
+      double th = theta;
+      for (int nt = 0; nt < 5; ++nt) {
+        fold_apply(c, prec, u.c(), 1, &th, R.c(), D.c());
+        cplx* part = dots.c() + 8;
+        ts_dot(s, u.c(), 1, MU.c(), 1, N1, part, dots.c(), 1, true);
+        ts_dot(s, u.c(), 1, R.c(), 1, N1, part, dots.c() + 1, 1, true);
+        ts_dot(s, u.c(), 1, D.c(), 1, N1, part, dots.c() + 2, 1, true);
+        cplx hv[3];
+        CVS_CUDA(cudaMemcpyAsync(hv, dots.p, sizeof hv, cudaMemcpyDeviceToHost, s));
+        c->sync();
+        const double lam = hv[0].x + hv[1].x, nn = std::max(0.0, hv[2].x);
+        double tn = th + (lam - th) / (1.0 + nn);
+        if (!std::isfinite(tn)) break;
+        tn = std::min(tn, 0.5 * (th + pole));
+        const bool done = std::fabs(tn - th) < 1e-4 * std::max(1.0, std::fabs(th));
+        th = tn;
+        if (done) break;
+      }
+      if (verbose())
+        fprintf(stderr, "[cvsadc] schur (large) theta %.6f lam0 %.6f -> next theta %.6f\n",
+                theta, lam0, th);
+      theta = th;
+    }
+    c->sync();
+    c->sch_ms = now_ms() - t0;
+    return c->sch_on;
   }
   // theta0: after each full build of S(theta), Newton's method runs on
   // lam0 of S projected on its p lowest eigenvectors u_i, where for any
@@ -1150,7 +1368,7 @@ bool schur_setup(cvsadc_ctx* c) {
     ok = true;
     // W = M21 U_p and A_p = U_p^H M11 U_p
     CVS_CUDA(cudaMemsetAsync(xb.p, 0, (size_t)pp * N * sizeof(cplx), s));
-    copyv(c, pp, (int)N1, 1.0, view(c->sch_U.c(), 1, N1), view(xb.p, N, 1));
+    copyv(c, pp, (int)N1, 1.0, view(c->sch_U.c(), 1, c->sch_p), view(xb.p, N, 1));
     sigma_impl(c, prec, xb.c(), wb.c(), pp, SIG_FWD);
     c->sch_couplings += pp;
     cplx* Gw = gb.c();
@@ -1235,7 +1453,7 @@ DavResult davidson_impl(cvsadc_ctx* c, int prec, int nroots, int max_iter,
                         int max_sub, double tol, const cplx* X0, int nx0,
                         cplx* Xout, double* wout,
                         bool stop_on_stagnation = false, bool schur = false) {
-  schur = schur && c->sch_on;
+  schur = schur && c->sch_on && c->sch_p == c->N1;
   // Gram matrices, Gram-Schmidt and Ritz combinations: plain FP64 for the
   // FP64-class precisions, double-float on the FP32 pipes for the mixed ones
   const bool a64 = prec == CVSADC_FP64 || prec == CVSADC_FP64_SLICE7;
@@ -1749,8 +1967,8 @@ FoldResult folded_davidson(cvsadc_ctx* c, int prec, int k, int max_iter, int max
   } else {
     CVS_REQUIRE(c->sch_on, CVSADC_EINVAL, "folded solver: no initial vectors");
     // the lowest eigenvectors of S(theta0), lifted at theta0
-    nguess = (int)std::min<int64_t>(std::min(2 * k, msub), N1);
-    copyv(c, nguess, (int)N1, 1.0, view(c->sch_U.c(), 1, N1), view(T, N1, 1));
+    nguess = (int)std::min<int64_t>(std::min(std::min(2 * k, msub), c->sch_p), N1);
+    copyv(c, nguess, (int)N1, 1.0, view(c->sch_U.c(), 1, c->sch_p), view(T, N1, 1));
     std::vector<double> t0(nguess, c->sch_theta);
     restart(T, t0.data(), nguess);
     --res.restarts;
@@ -1774,6 +1992,17 @@ FoldResult folded_davidson(cvsadc_ctx* c, int prec, int k, int max_iter, int max
       const double nq = hd[(size_t)q * msub + q].x;
       est[q] = th[q] + (lam - th[q]) / (1.0 + nq);
       if (!std::isfinite(est[q])) est[q] = th[q];
+    }
+    if (c->sch_on && x0 == nullptr) {
+      // first-order drift of the Schur eigenvalues with theta: d_i = ||W(theta0)
+      // M21 u_i||^2 for the guesses u_i (lifted at theta0 just now); the
+      // higher eigenvectors take the last of these
+      std::vector<double> dd(c->sch_p, std::max(0.0, hd[(size_t)(m - 1) * msub + (m - 1)].x));
+      for (int q = 0; q < m && q < c->sch_p; ++q) dd[q] = std::max(0.0, hd[(size_t)q * msub + q].x);
+      c->sch_d.ensure((size_t)c->sch_p * sizeof(double));
+      CVS_CUDA(cudaMemcpyAsync(c->sch_d.p, dd.data(), c->sch_p * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+      c->sch_d_on = true;
     }
     CVS_CUDA(cudaMemcpyAsync(T, V, (size_t)m * N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
     restart(T, est.data(), m);
@@ -1867,13 +2096,44 @@ FoldResult folded_davidson(cvsadc_ctx* c, int prec, int k, int max_iter, int max
                                  N1 * sizeof(cplx), cudaMemcpyDeviceToDevice, s));
     std::vector<double> wt(cnt);
     for (int q = 0; q < cnt; ++q) wt[q] = w[todo[q]];
-    if (c->sch_on) {
+    if (c->sch_on && c->sch_p < N1) {
+      // partial eigensystem: t = U_p (w - lam)^-1 U_p^H r~ plus
+      // (1 - U_p U_p^H) r~ / (w - lam_c), lam_c the highest computed
+      const int pp = c->sch_p;
+      double lam_c = 0.0;
+      CVS_CUDA(cudaMemcpyAsync(&lam_c, c->sch_lam.d() + pp - 1, sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+      cplx* Ty = c->sch_tmp.c();
+      CVS_CUDA(cudaMemcpyAsync(rn1, wt.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+      c->sync();
+      gemm64(c, pp, cnt, (int)N1, 1.0, conj_of(trans(view(c->sch_U.c(), pp, 1))),
+             view(Rt, 1, N1), 0.0, view(Ty, cnt, 1));
+      if (!c->sch_d_on) {
+        c->sch_d.ensure((size_t)pp * sizeof(double));
+        CVS_CUDA(cudaMemsetAsync(c->sch_d.p, 0, (size_t)pp * sizeof(double), s));
+        c->sch_d_on = true;
+      }
+      eig_shift_partial(s, Ty, pp, cnt, c->sch_lam.d(), c->sch_d.d(), c->sch_theta, rn1, lam_c);
+      gemm64(c, (int)N1, cnt, pp, 1.0, view(c->sch_U.c(), pp, 1), view(Ty, cnt, 1), 0.0,
+             view(T, 1, N1));
+      std::vector<double> sc(cnt);
+      for (int q = 0; q < cnt; ++q) {
+        const double dc = wt[q] - lam_c;
+        sc[q] = -1.0 / (std::fabs(dc) < 1e-8 ? (dc < 0 ? -1e-8 : 1e-8) : dc);
+      }
+      CVS_CUDA(cudaMemcpyAsync(rnt, sc.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, s));
+      row_axpy(s, T, Rt, rnt, cnt, N1, T);
+      c->sync();
+    } else if (c->sch_on) {
       // t = U (w - lam)^-1 U^H r~   (S(theta0) = U diag(lam) U^H)
       cplx* Ty = c->sch_tmp.c();
       CVS_CUDA(cudaMemcpyAsync(rn1, wt.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, s));
       gemm64(c, (int)N1, cnt, (int)N1, 1.0, conj_of(trans(view(c->sch_U.c(), N1, 1))),
              view(Rt, 1, N1), 0.0, view(Ty, cnt, 1));
-      eig_shift(s, Ty, N1, cnt, c->sch_lam.d(), rn1);
+      if (c->sch_d_on)
+        eig_shift_d(s, Ty, N1, cnt, c->sch_lam.d(), c->sch_d.d(), c->sch_theta, rn1);
+      else
+        eig_shift(s, Ty, N1, cnt, c->sch_lam.d(), rn1);
       gemm64(c, (int)N1, cnt, (int)N1, 1.0, view(c->sch_U.c(), N1, 1), view(Ty, cnt, 1), 0.0,
              view(T, 1, N1));
     } else {
@@ -1947,6 +2207,7 @@ void folded_entry(cvsadc_ctx* c, const cvsadc_params* p, double* omega, void* X,
   c->sch_builds = 0;
   c->sch_couplings = 0;
   const bool use_schur = (p->flags & CVSADC_FLAG_DIAG_PRECOND) == 0;
+  c->sch_d_on = false;
   if (!(use_schur && schur_setup(c))) c->sch_on = false;
   const int prec = p->precision;
   const bool refine = needs_refine(prec) && (p->flags & CVSADC_FLAG_NO_REFINE) == 0;
@@ -2501,12 +2762,12 @@ double estimate_bytes(const cvsadc_params* p) {
   // Schur-complement preconditioner (when the singles space allows it)
   if (N1 <= 4096 && !(p->flags & CVSADC_FLAG_DIAG_PRECOND)) {
     const double v3 = v * v * v;
-    const double per_j = (3.0 + nc) * v3 * z;
+    const double per_j = (2.0 + nc) * v3 * z;
     const double jc = std::max(1.0, std::min(nw, std::floor(6e9 / per_j)));
     b += z * (nc * v * nc * nw * 2 + nc * nc * v * nw);  // <Kb||Ij>, temps
     b += std::min(nw * v3 * z, 48e9);          // cached <ab||cj>
     b += 4 * z * N1 * N1 + 8 * N1 + z * nc * v * v + z * v * v * nc * nc;
-    b += (3.0 + nc) * jc * v3 * z;             // chunk workspace
+    b += (2.0 + nc) * jc * v3 * z;             // chunk workspace
     b += z * std::max(v * v * nc * nc, N1 * 64.0) + 8 * (800 + 2 * N1) + 2 * z * N;
   }
   return 1.1 * b + (64 << 20);
