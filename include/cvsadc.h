@@ -355,6 +355,21 @@ int cvsadc_zgemm_small_noalloc(void* cuda_stream, int32_t M, int32_t N,
                                const void* B, int64_t ldb, void* C,
                                int64_t ldc);
 
+/* Broadened spectrum (sections "Computational Details" and "Results and
+ * Discussion": computed spectra are sums of Lorentzian lines of a given
+ * FWHM, 0.3 eV in most figures, moved by one uniform energy shift to align
+ * an edge with experiment):
+ *   out[g] = sum_n osc[n] L(E_g - (omega[n] * 27.211386245988 + shift_ev)),
+ *   E_g = e0_ev + g de_ev (g < npts),
+ *   L(x) = (h / pi) / (x^2 + h^2), h = fwhm_ev / 2 (unit area).
+ * omega [nroots] in Hartree (as cvsadc_solve returns them), osc [nroots],
+ * out [npts]; host pointers unless flags has CVSADC_FLAG_DEVICE_PTRS.
+ * Computed on the context's stream.  Errors: CVSADC_EINVAL for NULL arrays
+ * with positive sizes, negative sizes or fwhm_ev <= 0; CVSADC_ECUDA. */
+int cvsadc_spectrum(cvsadc_ctx* ctx, int32_t flags, int32_t nroots, const double* omega,
+                    const double* osc, double e0_ev, double de_ev, int32_t npts,
+                    double fwhm_ev, double shift_ev, double* out);
+
 /* Block inner products out[i][j] = sum_n conj(A[i][n]) B[j][n] (i < ma,
  * j < mb; out host [ma][mb] complex128) of device vectors A [ma][N] and
  * B [mb][N] (complex128, on the context's device), in the arithmetic the

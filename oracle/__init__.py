@@ -14,6 +14,8 @@ Modules:
                    matrix-free sigma, transition moments, eigen-solvers;
 * ``fci``       -- determinant-space engine and brute-force ISR, the
                    independent pin of the ``adc2`` element formulas;
+* ``spectrum``  -- Lorentzian-broadened spectrum from roots and oscillator
+                   strengths;
 * ``grad``      -- the gradient of a sum of roots with respect to the spinor
                    energies and the Cholesky vectors, by torch autograd of
                    the explicit matrix (CPU, complex128), pinned by central

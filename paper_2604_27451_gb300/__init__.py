@@ -205,6 +205,18 @@ class Context:
                                           pc, N))
         return C
 
+    def spectrum(self, omega, osc, e0_ev, de_ev, npts, fwhm_ev=0.3, shift_ev=0.0):
+        """Lorentzian-broadened spectrum (numpy [npts]) of roots omega (Eh)
+        and oscillator strengths osc on the grid e0_ev + g de_ev."""
+        w = np.ascontiguousarray(np.asarray(omega, dtype=np.float64))
+        f = np.ascontiguousarray(np.asarray(osc, dtype=np.float64))
+        out = np.empty(int(npts))
+        self._check(self.lib.cvsadc_spectrum(
+            self.h, 0, w.size, ctypes.c_void_p(w.ctypes.data), ctypes.c_void_p(f.ctypes.data),
+            float(e0_ev), float(de_ev), int(npts), float(fwhm_ev), float(shift_ev),
+            ctypes.c_void_p(out.ctypes.data)))
+        return out
+
     def block_dot(self, A, B, precision="fp64"):
         """A^H B (numpy [ma][mb]) of torch CUDA blocks A [ma][N], B [mb][N]
         in the Davidson solver's arithmetic for `precision`."""

@@ -95,6 +95,9 @@ _SIGNATURES = {
                                                   ctypes.c_int32, _vp, ctypes.c_int64,
                                                   _vp, ctypes.c_int64, _vp,
                                                   ctypes.c_int64]),
+    "cvsadc_spectrum": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                                       ctypes.c_double, ctypes.c_double, _vp]),
     "cvsadc_block_dot": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp,
                                         ctypes.c_int32, ctypes.c_int64, _vp]),
     "cvsadc_launch_count": (ctypes.c_int64, []),

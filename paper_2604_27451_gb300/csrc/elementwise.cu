@@ -885,6 +885,32 @@ void t2_band_inplace(cudaStream_t s, cplx* X, cplx* T, int a0, int nb, int o,
   CVS_CHECK_LAUNCH();
 }
 
+// I(E_g) = sum_n f_n (h / pi) / ((E_g - E_n)^2 + h^2), E_g = e0 + g de,
+// E_n = omega_n * ev_per_eh + shift, h = fwhm / 2; one grid point per thread
+__global__ void lorentz_kernel(const double* __restrict__ omega,
+                               const double* __restrict__ f, int nroots, double e0,
+                               double de, int npts, double h, double shift,
+                               double ev_per_eh, double* __restrict__ out) {
+  const double inv_pi = 0.318309886183790671537767526745;
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < npts; g += gridDim.x * blockDim.x) {
+    const double E = e0 + g * de;
+    double acc = 0.0;
+    for (int r = 0; r < nroots; ++r) {
+      const double x = E - (omega[r] * ev_per_eh + shift);
+      acc += f[r] * h / (x * x + h * h);
+    }
+    out[g] = acc * inv_pi;
+  }
+}
+
+void lorentz_spectrum(cudaStream_t s, const double* omega, const double* f, int nroots,
+                      double e0, double de, int npts, double fwhm, double shift,
+                      double ev_per_eh, double* out) {
+  lorentz_kernel<<<grid1d(npts, 256), 256, 0, s>>>(omega, f, nroots, e0, de, npts,
+                                                   0.5 * fwhm, shift, ev_per_eh, out);
+  CVS_CHECK_LAUNCH();
+}
+
 void reduce_sum(cudaStream_t s, const double* in, int n, double* out) {
   reduce_sum_kernel<<<1, 256, 0, s>>>(in, n, out);
   CVS_CHECK_LAUNCH();

@@ -68,6 +68,10 @@ void t2_band(cudaStream_t s, const cplx* V, int a0, int na, int o, int v,
 int64_t t2_band_ip_blocks(int nb, int o, int v);
 void t2_band_inplace(cudaStream_t s, cplx* X, cplx* T, int a0, int nb, int o,
                      int v, const double* eps, double* part, double* emp2);
+// Lorentzian-broadened spectrum on a uniform grid (see cvsadc_spectrum)
+void lorentz_spectrum(cudaStream_t s, const double* omega, const double* f, int nroots,
+                      double e0, double de, int npts, double fwhm, double shift,
+                      double ev_per_eh, double* out);
 // Deterministic sum of n doubles into *out (device).
 void reduce_sum(cudaStream_t s, const double* in, int n, double* out);
 

@@ -3098,6 +3098,30 @@ int cvsadc_zgemm(cvsadc_ctx* c, int32_t precision, int32_t flags, int32_t M,
   });
 }
 
+int cvsadc_spectrum(cvsadc_ctx* c, int32_t flags, int32_t nroots, const double* omega,
+                    const double* osc, double e0_ev, double de_ev, int32_t npts,
+                    double fwhm_ev, double shift_ev, double* out) {
+  if (!c || nroots < 0 || npts < 0 || (nroots > 0 && (!omega || !osc)) ||
+      (npts > 0 && !out) || !(fwhm_ev > 0.0))
+    return CVSADC_EINVAL;
+  return guarded(c, [&] {
+    if (npts == 0) return;
+    const bool dev = (flags & CVSADC_FLAG_DEVICE_PTRS) != 0;
+    DBuf w, f, o;
+    w.ensure((size_t)(nroots + 1) * sizeof(double));
+    f.ensure((size_t)(nroots + 1) * sizeof(double));
+    o.ensure((size_t)npts * sizeof(double));
+    if (nroots > 0) {
+      upload(c, w, omega, nroots * sizeof(double), dev);
+      upload(c, f, osc, nroots * sizeof(double), dev);
+    }
+    lorentz_spectrum(c->stream, w.d(), f.d(), nroots, e0_ev, de_ev, npts, fwhm_ev, shift_ev,
+                     27.211386245988, o.d());
+    download(c, out, o.p, (size_t)npts * sizeof(double), dev);
+    c->sync();
+  });
+}
+
 int cvsadc_block_dot(cvsadc_ctx* c, int32_t precision, const void* A,
                      int32_t ma, const void* B, int32_t mb, int64_t N, void* out) {
   if (!c || !A || !B || !out || ma < 1 || mb < 1 || N < 1) return CVSADC_EINVAL;

@@ -120,3 +120,21 @@ def test_folded_large_singles_space():
         r = np.concatenate([s1, s2]) - out["omega"][q] * x
         assert np.linalg.norm(r) < 1e-6, (q, np.linalg.norm(r))
     ctx.close()
+
+
+def test_spectrum_matches_oracle():
+    """The broadened spectrum of the small workload's roots and oscillator
+    strengths (FWHM 0.3 eV, a -4.1 eV shift) against the oracle's sum of
+    Lorentzians, to 1e-12 of its maximum."""
+    import paper_2604_27451_gb300 as pkg
+    from oracle import spectrum
+
+    g = json.load(open(os.path.join(GOLDEN, "small_fp64.json")))
+    om, f = np.array(g["omega"]), np.array(g["osc"])
+    ctx = pkg.Context(0)
+    e0, de, n = 400.0, 0.01, 6001
+    got = ctx.spectrum(om, f, e0, de, n, 0.3, -4.1)
+    ref = spectrum.lorentzian_spectrum(om, f, e0 + de * np.arange(n), 0.3, -4.1)
+    assert np.abs(got - ref).max() < 1e-12 * ref.max()
+    assert np.abs(ctx.spectrum([], [], e0, de, 3) ).max() == 0.0
+    ctx.close()

@@ -14,7 +14,7 @@ import itertools
 import numpy as np
 import pytest
 
-from oracle import adc2, fns, mp2
+from oracle import adc2, fns, mp2, spectrum
 from oracle.fci import DetSpace, ISR, apply_string, full_antisym_integrals
 from oracle.integrals import antisym
 from synth import make_instance, make_kramers_instance, make_spinfree_instance
@@ -446,3 +446,28 @@ def test_self_energy_splits_into_five_structured_terms():
     S -= np.einsum("Ijcd,KdIj,EcIj->KcEd", w, h.conj(), h)
     S = S.reshape(nc * nv, nc * nv)
     assert np.abs(S - explicit).max() < 1e-13 * np.abs(explicit).max()
+
+
+# ---------------------------------------------------- N4 broadened spectrum
+
+def test_lorentzian_spectrum_closed_forms():
+    rng = np.random.default_rng(8)
+    om = rng.uniform(15.0, 16.0, 5)
+    f = rng.uniform(0.1, 2.0, 5)
+    g, shift = 0.3, -4.1
+    a, b = 380.0, 460.0
+    grid = np.linspace(a, b, 400001)
+    I = spectrum.lorentzian_spectrum(om, f, grid, g, shift)
+    # integral over [a, b]: closed form of the arctangent
+    E = om * spectrum.EV_PER_EH + shift
+    h = g / 2
+    exact = np.sum(f * (np.arctan((b - E) / h) - np.arctan((a - E) / h))) / np.pi
+    trap = np.sum(0.5 * (I[1:] + I[:-1]) * np.diff(grid))
+    assert abs(trap - exact) < 1e-8 * exact
+    # one line: peak 2 f / (pi g) at E, half of it at E +- g/2
+    one = spectrum.lorentzian_spectrum([om[0]], [f[0]], [E[0], E[0] - h, E[0] + h], g, shift)
+    assert abs(one[0] - 2 * f[0] / (np.pi * g)) < 1e-12 * one[0]
+    assert np.abs(one[1:] - 0.5 * one[0]).max() < 1e-12 * one[0]
+    # linear in the strengths
+    I2 = spectrum.lorentzian_spectrum(om, 3 * f, grid[::1000], g, shift)
+    assert np.abs(I2 - 3 * I[::1000]).max() < 1e-12 * np.abs(I2).max()
