@@ -751,85 +751,116 @@ __global__ void __launch_bounds__(576, 1)
                  "r"(2 * SBN));
 }
 
-// per-row (A: rows m, max over k) exponent: max |re|, |im| < 2^e
+// Exponents and slices work on the IEEE bits with integer arithmetic (this
+// GPU runs FP64 at a small fraction of its integer and FP32 rates).  For a
+// normal double the biased exponent field E gives |x| < 2^(E - 1022); zeros
+// and subnormals count as 0.
+
+__device__ __forceinline__ int exp_field(double x) {
+  return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+
+// column offset of a view for an int column index (32-bit index math)
+__device__ __forceinline__ int64_t vcol32(const View& v, int c) {
+  if (v.c_lo == INT32_MAX) return (int64_t)c * v.cs_lo;
+  const int h = c / v.c_lo;
+  return (int64_t)h * v.cs_hi + (int64_t)(c - h * v.c_lo) * v.cs_lo;
+}
+
+// per-row (A: rows m, max over k) exponent e with max |re|, |im| < 2^e (0
+// for an all-zero row); one warp per row
 __global__ void row_exp_kernel(View A, int M, int K, int k0, int* e) {
-  for (int m = blockIdx.x; m < M; m += gridDim.x) {
-    double mx = 0.0;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  for (int m = warp; m < M; m += nwarp) {
     const int64_t ro = vrow(A, m);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      cplx a = A.p[ro + vcol(A, k0 + k)];
-      mx = fmax(mx, fmax(fabs(a.x), fabs(a.y)));
+    int mx = 0;
+    for (int k = lane; k < K; k += 32) {
+      const cplx a = A.p[ro + vcol32(A, k0 + k)];
+      mx = max(mx, max(exp_field(a.x), exp_field(a.y)));
     }
-    __shared__ double red[256];
-    red[threadIdx.x] = mx;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) e[m] = red[0] > 0 ? ilogb(red[0]) + 1 : 0;
-    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) e[m] = mx > 0 ? mx - 1022 : 0;
   }
 }
 
 // per-column (B: columns n, max over k) exponent
 __global__ void col_exp_kernel(View B, int K, int k0, int N, int* e) {
   for (int n = blockIdx.x; n < N; n += gridDim.x) {
-    double mx = 0.0;
+    int mx = 0;
     const int64_t co = vcol(B, n);
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      cplx b = B.p[vrow(B, k0 + k) + co];
-      mx = fmax(mx, fmax(fabs(b.x), fabs(b.y)));
+      const cplx b = B.p[vrow(B, k0 + k) + co];
+      mx = max(mx, max(exp_field(b.x), exp_field(b.y)));
     }
-    __shared__ double red[256];
+    __shared__ int red[256];
     red[threadIdx.x] = mx;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+      if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
       __syncthreads();
     }
-    if (threadIdx.x == 0) e[n] = red[0] > 0 ? ilogb(red[0]) + 1 : 0;
+    if (threadIdx.x == 0) e[n] = red[0] > 0 ? red[0] - 1022 : 0;
     __syncthreads();
   }
 }
 
+// S balanced 7-bit slices of t = x 2^-e (|t| < 1): T = round(t 2^(7S))
+// in integer arithmetic, then digits q_{S-1} .. q_1 in [-64, 63] from the
+// bottom and q_0 = the rest, in [-128, 128], so that
+// t = sum_i q_i 2^(-7(i+1)) + r with |r| <= 2^(-7S-1); each q_i is exact
+// in bf16.
 template <int S>
 __device__ __forceinline__ void slices(double x, int e, __nv_bfloat16* q) {
-  double t = ldexp(x, -e);
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    t *= (double)(1 << SLICE_BITS);
-    double r = rint(t);
-    q[i] = __double2bfloat16(r);  // |r| <= 128: exact
-    t -= r;
+  const long long bits = __double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long T = 0;
+  if (E != 0) {
+    const long long m = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = E - 1075 - e + SLICE_BITS * S;
+    if (sh >= 0)
+      T = m << sh;
+    else if (sh > -63)
+      T = (m + (1LL << (-sh - 1))) >> (-sh);
+    if (bits < 0) T = -T;
   }
+#pragma unroll
+  for (int i = S - 1; i > 0; --i) {
+    const long long d = ((T + 64) & 127) - 64;
+    q[i] = __float2bfloat16_rn((float)d);
+    T = (T - d) >> SLICE_BITS;
+  }
+  q[0] = __float2bfloat16_rn((float)T);
 }
 
+// A' [Mp][2 npairs Kp]: row m, segment 2p + {0: re, 1: im} of slice c_si[p];
+// one warp per row, lanes along k
 template <int S>
 __global__ void slice_pack_a(View A, int M, int K, int k0, int Mp, int Kp,
                              int npairs, const int* __restrict__ eA,
                              __nv_bfloat16* out) {
   const int64_t ld = (int64_t)2 * npairs * Kp;
-  const int64_t total = (int64_t)Mp * Kp;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int m = idx / Kp, k = idx % Kp;
-    cplx a = cmake(0, 0);
-    int e = 0;
-    if (m < M) {
-      e = eA[m];
-      if (k < K) {
-        a = A.p[vrow(A, m) + vcol(A, k0 + k)];
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  for (int m = warp; m < Mp; m += nwarp) {
+    const bool live = m < M;
+    const int64_t ro = live ? vrow(A, m) : 0;
+    const int e = live ? eA[m] : 0;
+    __nv_bfloat16* o = out + (int64_t)m * ld;
+    for (int k = lane; k < Kp; k += 32) {
+      cplx a = cmake(0, 0);
+      if (live && k < K) {
+        a = A.p[ro + vcol32(A, k0 + k)];
         if (A.conj) a.y = -a.y;
       }
-    }
-    __nv_bfloat16 re[S], im[S];
-    slices<S>(a.x, e, re);
-    slices<S>(a.y, e, im);
-    __nv_bfloat16* o = out + (int64_t)m * ld + k;
-    for (int p = 0; p < npairs; ++p) {
-      o[(2 * p) * (int64_t)Kp] = re[c_si[p]];
-      o[(2 * p + 1) * (int64_t)Kp] = im[c_si[p]];
+      __nv_bfloat16 re[S], im[S];
+      slices<S>(a.x, e, re);
+      slices<S>(a.y, e, im);
+      for (int p = 0; p < npairs; ++p) {
+        o[(2 * p) * (int64_t)Kp + k] = re[c_si[p]];
+        o[(2 * p + 1) * (int64_t)Kp + k] = im[c_si[p]];
+      }
     }
   }
 }
@@ -935,13 +966,14 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
     __nv_bfloat16* bpc = bc ? (__nv_bfloat16*)((char*)bc->base + ci * d.b_bytes) : bp;
     int* eBc = bc ? (int*)((char*)bc->base + nch * d.b_bytes) + ci * eb_n : eB;
     const bool pack_b = !bc || !bc->filled;
-    row_exp_kernel<<<std::min(M, 152 * 16), 256, 0, s>>>(A, M, Kc, k0, eA);
+    row_exp_kernel<<<(unsigned)std::min<int64_t>((M + 7) / 8, 152 * 32), 256, 0, s>>>(
+        A, M, Kc, k0, eA);
     CVS_CHECK_LAUNCH();
     if (pack_b) {
       col_exp_kernel<<<std::min(N, 152 * 16), 256, 0, s>>>(B, Kc, k0, N, eBc);
       CVS_CHECK_LAUNCH();
     }
-    const unsigned ga = grid1d((int64_t)d.Mp * Kp, 256);
+    const unsigned ga = (unsigned)std::min<int64_t>((d.Mp + 7) / 8, 152 * 32);
     const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * Kp, 256);
     if (nslices == 4) {
       slice_pack_a<4><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, d.npairs, eA, ap);
