@@ -113,14 +113,15 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait on the phase with the given parity
+// bounded wait on the phase with the given parity: try_wait suspends the
+// thread in hardware for a while before it reports "not yet", so the loop
+// polls without sleeping and reads the clock only every 64 tries
 __device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   if (mbar_try(bar, parity)) return true;
-  uint64_t t0 = gtime();
-  while (true) {
+  const uint64_t t0 = gtime();
+  for (uint32_t n = 1;; ++n) {
     if (mbar_try(bar, parity)) return true;
-    if (gtime() - t0 > WAIT_NS) return false;
-    __nanosleep(64);
+    if ((n & 63) == 0 && gtime() - t0 > WAIT_NS) return false;
   }
 }
 __device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar,
@@ -546,7 +547,7 @@ void zgemm_tc(cudaStream_t s, int nprod, int M, int N, int K, double alpha,
 namespace {
 
 constexpr int SBN = 128;          // N' per CTA (64 complex columns)
-constexpr int SSTAGES = 6;
+constexpr int SSTAGES = 7;
 constexpr int S_A_TILE = BM * BK * 2;
 constexpr int S_B_TILE = SBN * BK * 2;
 constexpr int S_STAGE = S_A_TILE + S_B_TILE;
