@@ -164,10 +164,11 @@ def measured_peaks():
                 "fallback": True}
 
 
-def traffic_from_profile():
-    """Per-launch DRAM bytes of the slice GEMM from the committed ncu summary
-    (None when absent)."""
-    p = os.path.join(ROOT, "profiles", "tc_slice_kernel_medium_sigma.md")
+def traffic_from_profile(kernel):
+    """Per-launch DRAM bytes of one kernel at the bench's launch shape, from
+    its committed ncu summary profiles/<kernel>_large_sigma.md (None when
+    absent or recorded as null)."""
+    p = os.path.join(ROOT, "profiles", "%s_large_sigma.md" % kernel)
     try:
         for line in open(p):
             if line.startswith("traffic_bytes_per_launch:"):
@@ -328,10 +329,12 @@ def run_ours(args):
     if cnt.value > 0 and prec in PRODUCTS:
         achieved = kfl.value / (kms.value / 1e3) / 1e12
         peak = peaks["bf16_tflops"] / PRODUCTS[prec]
+        kname = {"slice4": "tc_slice4r_kernel", "fp64_slice7": "tc_slice_kernel",
+                 "bf16x3": "tc_gemm_kernel"}[prec]
         roofline = {"bound": "tensor", "achieved": round(achieved, 2), "peak": round(peak, 2),
                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                    "traffic": traffic_from_profile(),
-                    "kernel": "tc_slice_kernel" if prec != "bf16x3" else "tc_gemm_kernel",
+                    "traffic": traffic_from_profile(kname),
+                    "kernel": kname,
                     "launches": int(cnt.value), "avg_launch_ms": round(kms.value / cnt.value, 4),
                     "share_of_step_time": round(kms.value / ms_total, 4),
                     "peak_basis": "measured bf16 burst %.1f TFLOP/s / %d bf16 products per "

@@ -899,21 +899,290 @@ __global__ void slice_pack_b(View B, int K, int k0, int N, int Np2, int Kp,
   }
 }
 
+// ---------------------------------------------------------------------------
+// SLICE4 with slice reuse.  The packed operands hold each slice once: A''
+// row m = 8 segments (slice i, re / im) of Kp values; B'' rows 2n (the real
+// output column) and 2n+1 (the imaginary one) = 8 segments (slice j,
+// re-part / im-part: [re b, -im b] for row 2n and [im b, re b] for row
+// 2n+1).  One pipeline stage is one K block of 64 in one part c (re or im):
+// the four A tiles A_{i,c} (128 x 64) and four B tiles B_{j,c} (64 x 64),
+// 96 KB, from which all ten slice pairs are issued.  Pairs of one order
+// o = i + j share the scale 2^{-7(o+2)} and one tensor-memory accumulator;
+// a run is 2 K blocks x 2 parts: at most 4 pairs x 256 products of
+// |q q'| <= 2^13 (2^14 for order 0, one pair) per element, so every run
+// sums exactly in FP32.  TMEM: 2 buffers x 4 orders x 64 columns = 512.
+// The drain adds each order, times its scale, to float-float accumulators.
+//
+// CTA: 576 threads, tile 128 x 64 (N' = 64: 32 complex columns).  Warp 0
+// lane 0: TMA producer; warp 1 lane 0: MMA issuer; warps 2..17: drain (warp
+// w reads TMEM lanes 32 (w % 4) .. +31 and the 16 columns [16 c, 16 c + 16),
+// c = (w - 2) / 4, of every order).
+// ---------------------------------------------------------------------------
+constexpr int RBN = 64;                  // N' per CTA
+constexpr int R_A_TILE = BM * BK * 2;    // 16 KB
+constexpr int R_B_TILE = RBN * BK * 2;   // 8 KB
+constexpr int R_STAGE = 4 * R_A_TILE + 4 * R_B_TILE;  // 96 KB
+constexpr int R_STAGES = 2;
+constexpr int R_SMEM = R_STAGES * R_STAGE + 1024 + 512;
+constexpr int R_RUN = 4;                 // units (K block, part) per exact run
+
+__global__ void __launch_bounds__(576, 1)
+    tc_slice4r_kernel(const __grid_constant__ CUtensorMap tmA,
+                      const __grid_constant__ CUtensorMap tmB, int Kp, int nkb,
+                      int zl, int M, int N, const int* __restrict__ eA,
+                      const int* __restrict__ eB, double alpha, double beta,
+                      View C, cplx* part, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + R_STAGES * R_STAGE);
+  uint64_t* empty = full + R_STAGES;
+  uint64_t* afull = empty + R_STAGES;  // [2]
+  uint64_t* aempty = afull + 2;        // [2]
+  uint32_t* tslot = (uint32_t*)(aempty + 2);
+  __shared__ int fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int mt, nt;
+  tile_coords(mt, nt);
+  const int m0 = mt * BM, n0 = nt * RBN;
+  const int z = blockIdx.z;
+  // this CTA's K blocks [kb0, kb1); units u = 2 (kb - kb0) + c
+  const int kb0 = z * zl, kb1 = min(nkb, kb0 + zl);
+  const int nunits = 2 * max(0, kb1 - kb0);
+  const int nruns = (nunits + R_RUN - 1) / R_RUN;
+
+  if (threadIdx.x == 0) {
+    fail = 0;
+    for (int s = 0; s < R_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&afull[b], 1);
+      mbar_init(&aempty[b], 16);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile(
+        "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+            smem_u32(tslot)),
+        "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (threadIdx.x == 0) {
+    // TMA producer: unit u -> K block kb0 + u / 2, part c = u % 2
+    for (int u = 0; u < nunits; ++u) {
+      const int s = u % R_STAGES;
+      const uint32_t ph = (u / R_STAGES) & 1;
+      if (u >= R_STAGES && !mbar_wait(&empty[s], ph ^ 1)) {
+        fail = 1;
+        break;
+      }
+      if (fail) break;
+      const int kb = kb0 + u / 2, c = u & 1;
+      uint8_t* st = smem + s * R_STAGE;
+      mbar_expect_tx(&full[s], R_STAGE);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        tma_load(&tmA, &full[s], st + i * R_A_TILE, (2 * i + c) * Kp + kb * BK, m0);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        tma_load(&tmB, &full[s], st + 4 * R_A_TILE + j * R_B_TILE,
+                 (2 * j + c) * Kp + kb * BK, n0);
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer: for each unit, the ten pairs into their order's
+    // accumulator of the run's buffer
+    const uint32_t id = idesc_bf16(BM, RBN);
+    for (int r = 0; r < nruns && !fail; ++r) {
+      const int b = r & 1;
+      if (r >= 2 && !mbar_wait(&aempty[b], ((r >> 1) + 1) & 1)) {
+        fail = 4;
+        break;
+      }
+      fence_after();
+      const int u0 = r * R_RUN, u1 = min(nunits, u0 + R_RUN);
+      for (int u = u0; u < u1; ++u) {
+        const int s = u % R_STAGES;
+        const uint32_t ph = (u / R_STAGES) & 1;
+        if (!mbar_wait(&full[s], ph)) {
+          fail = 2;
+          break;
+        }
+        fence_after();
+        const uint32_t st = smem_u32(smem + s * R_STAGE);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const uint32_t dt = tmem + (uint32_t)((b * 4 + o) * RBN);
+#pragma unroll
+          for (int i = 0; i <= o; ++i) {
+            const int j = o - i;
+            const uint64_t ad = sdesc(st + i * R_A_TILE);
+            const uint64_t bd = sdesc(st + 4 * R_A_TILE + j * R_B_TILE);
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk)
+              umma(dt, ad + 2 * kk, bd + 2 * kk, id,
+                   (u != u0 || i != 0 || kk != 0) ? 1u : 0u);
+          }
+        }
+        umma_commit(&empty[s]);
+      }
+      umma_commit(&afull[b]);
+    }
+  } else if (warp >= 2) {
+    // drain warps
+    const int q = warp & 3;          // TMEM lane quarter
+    const int cq = (warp - 2) >> 2;  // 16-column chunk of the 64
+    float hi[16], lo[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) hi[i] = lo[i] = 0.f;
+    bool ok = true;
+    for (int r = 0; r < nruns; ++r) {
+      const int b = r & 1;
+      if (!mbar_wait(&afull[b], (r >> 1) & 1)) {
+        ok = false;
+        break;
+      }
+      fence_after();
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const float sc = exp2f(-(float)(SLICE_BITS * (o + 2)));
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((b * 4 + o) * RBN + cq * 16), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) ff_add(hi[i], lo[i], v[i] * sc);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&aempty[b]))
+                     : "memory");
+      }
+    }
+    if (!ok || fail) {
+      if (lane == 0) atomicExch(err, fail ? fail : 3);
+    } else {
+      const int m = m0 + q * 32 + lane;
+      if (m < M) {
+        const int64_t ro = part ? 0 : vrow(C, m);
+        const double em = ldexp(1.0, eA[m]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int n = (n0 + cq * 16) / 2 + i;
+          if (n < N) {
+            const double sc = alpha * em * ldexp(1.0, eB[n]);
+            cplx o = cmake(sc * ((double)hi[2 * i] + (double)lo[2 * i]),
+                           sc * ((double)hi[2 * i + 1] + (double)lo[2 * i + 1]));
+            if (part) {
+              part[((int64_t)z * M + m) * N + n] = o;
+              continue;
+            }
+            cplx* d = C.p + ro + vcol(C, n);
+            if (beta != 0.0) {
+              const cplx old = *d;
+              o.x += beta * old.x;
+              o.y += beta * old.y;
+            }
+            *d = o;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// A'' [Mp][8 Kp]: segment 2 i + {0: re, 1: im} holds slice i
+__global__ void slice4r_pack_a(View A, int M, int K, int k0, int Mp, int Kp,
+                               const int* __restrict__ eA, __nv_bfloat16* out) {
+  const int64_t ld = (int64_t)8 * Kp;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  for (int m = warp; m < Mp; m += nwarp) {
+    const bool live = m < M;
+    const int64_t ro = live ? vrow(A, m) : 0;
+    const int e = live ? eA[m] : 0;
+    __nv_bfloat16* o = out + (int64_t)m * ld;
+    for (int k = lane; k < Kp; k += 32) {
+      cplx a = cmake(0, 0);
+      if (live && k < K) {
+        a = A.p[ro + vcol32(A, k0 + k)];
+        if (A.conj) a.y = -a.y;
+      }
+      __nv_bfloat16 re[4], im[4];
+      slices<4>(a.x, e, re);
+      slices<4>(a.y, e, im);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        o[(2 * i) * (int64_t)Kp + k] = re[i];
+        o[(2 * i + 1) * (int64_t)Kp + k] = im[i];
+      }
+    }
+  }
+}
+
+// B'' [Np2][8 Kp]: rows 2n and 2n + 1, segment 2 j + {0, 1} of slice j
+__global__ void slice4r_pack_b(View B, int K, int k0, int N, int Np2, int Kp,
+                               const int* __restrict__ eB, __nv_bfloat16* out) {
+  const int64_t ld = (int64_t)8 * Kp;
+  const int64_t total = (int64_t)(Np2 / 2) * Kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int n = (int)(idx / Kp), k = (int)(idx % Kp);
+    cplx b = cmake(0, 0);
+    int e = 0;
+    if (n < N) {
+      e = eB[n];
+      if (k < K) {
+        b = B.p[vrow(B, k0 + k) + vcol(B, n)];
+        if (B.conj) b.y = -b.y;
+      }
+    }
+    __nv_bfloat16 re[4], im[4];
+    slices<4>(b.x, e, re);
+    slices<4>(b.y, e, im);
+    __nv_bfloat16* o0 = out + (int64_t)(2 * n) * ld + k;
+    __nv_bfloat16* o1 = o0 + ld;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      o0[(2 * j) * (int64_t)Kp] = re[j];
+      o0[(2 * j + 1) * (int64_t)Kp] = __hneg(im[j]);
+      o1[(2 * j) * (int64_t)Kp] = im[j];
+      o1[(2 * j + 1) * (int64_t)Kp] = re[j];
+    }
+  }
+}
+
+// packed geometry: SLICE4 packs each slice once (8 segments, N' tiles of
+// 64, the slice-reuse kernel); SLICE7 packs one segment pair per slice pair
+// (56 segments, N' tiles of 128)
 struct SDims {
-  int Mp, Np2, npairs, kc;
+  int Mp, Np2, npairs, nseg, kc;
   size_t a_bytes, b_bytes, e_bytes;
 };
 SDims sdims_of(int M, int N, int K, int nslices) {
   SDims d;
+  const int tn = nslices == 4 ? RBN : SBN;
   d.Mp = (M + BM - 1) / BM * BM;
-  d.Np2 = (2 * N + SBN - 1) / SBN * SBN;
+  d.Np2 = (2 * N + tn - 1) / tn * tn;
   d.npairs = nslices * (nslices + 1) / 2;
-  const size_t per_k = (size_t)(d.Mp + d.Np2) * 2 * d.npairs * 2;
+  d.nseg = nslices == 4 ? 8 : 2 * d.npairs;
+  const size_t per_k = (size_t)(d.Mp + d.Np2) * d.nseg * 2;
   int64_t kc = (int64_t)(PACK_BUDGET / per_k) / BK * BK;
   kc = std::max<int64_t>(kc, BK);
   d.kc = (int)std::min<int64_t>(kc, ((int64_t)K + BK - 1) / BK * BK);
-  d.a_bytes = (size_t)d.Mp * 2 * d.npairs * d.kc * 2;
-  d.b_bytes = (size_t)d.Np2 * 2 * d.npairs * d.kc * 2;
+  d.a_bytes = (size_t)d.Mp * d.nseg * d.kc * 2;
+  d.b_bytes = (size_t)d.Np2 * d.nseg * d.kc * 2;
   d.e_bytes = ((size_t)d.Mp + d.Np2 / 2 + 64) * sizeof(int);
   return d;
 }
@@ -948,12 +1217,15 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
   std::call_once(attr, [] {
     cudaFuncSetAttribute(tc_slice_kernel,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, S_SMEM);
+    cudaFuncSetAttribute(tc_slice4r_kernel,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, R_SMEM);
   });
   __nv_bfloat16* ap = (__nv_bfloat16*)work;
   __nv_bfloat16* bp = (__nv_bfloat16*)((char*)work + d.a_bytes);
   int* eA = (int*)((char*)work + d.a_bytes + d.b_bytes);
   int* eB = eA + d.Mp;
-  const int64_t tiles = (int64_t)(d.Np2 / SBN) * (d.Mp / BM);
+  const bool reuse = nslices == 4;
+  const int64_t tiles = (int64_t)(d.Np2 / (reuse ? RBN : SBN)) * (d.Mp / BM);
   const int64_t nch = ((int64_t)K + d.kc - 1) / d.kc;
   const size_t eb_n = (size_t)d.Np2 / 2 + 64;
   CVS_REQUIRE(!bc || bc->bytes >= (size_t)nch * (d.b_bytes + eb_n * sizeof(int)),
@@ -976,11 +1248,11 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
     }
     const unsigned ga = (unsigned)std::min<int64_t>((d.Mp + 7) / 8, 152 * 32);
     const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * Kp, 256);
-    if (nslices == 4) {
-      slice_pack_a<4><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, d.npairs, eA, ap);
+    if (reuse) {
+      slice4r_pack_a<<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, eA, ap);
       CVS_CHECK_LAUNCH();
       if (pack_b) {
-        slice_pack_b<4><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eBc, bpc);
+        slice4r_pack_b<<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, eBc, bpc);
         CVS_CHECK_LAUNCH();
       }
     } else {
@@ -991,7 +1263,25 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
         CVS_CHECK_LAUNCH();
       }
     }
-    const int64_t kcols = (int64_t)2 * d.npairs * Kp;
+    const int64_t kcols = (int64_t)d.nseg * Kp;
+    const double beta_c = (k0 == 0) ? beta : 1.0;
+    if (reuse) {
+      CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
+      CUtensorMap mb = make_map(bpc, d.Np2, kcols, RBN);
+      const int nkb = Kp / BK;  // K blocks; a run spans two
+      int sp = tc_splits(tiles, nkb, 2 * (R_RUN / 2));
+      if (part == nullptr || (size_t)sp * M * N > part_elems) sp = 1;
+      const int zl = (nkb + sp - 1) / sp;
+      const int nz = (nkb + zl - 1) / zl;
+      dim3 grid(d.Np2 / RBN, d.Mp / BM, nz);
+      const int tok = kstats_begin(s, K_TC_SLICE, 8.0 * M * N * (double)Kc);
+      tc_slice4r_kernel<<<grid, 576, R_SMEM, s>>>(ma, mb, Kp, nkb, zl, M, N, eA, eBc, alpha,
+                                                  beta_c, C, nz > 1 ? part : nullptr, err);
+      CVS_CHECK_LAUNCH();
+      kstats_end(s, tok);
+      if (nz > 1) splitk_reduce(s, M, N, nz, part, beta_c, C);
+      continue;
+    }
     CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
     CUtensorMap mb = make_map(bpc, d.Np2, kcols, SBN);
     const int ktpp = 2 * Kp / BK;
@@ -999,7 +1289,6 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
     if (part == nullptr || (size_t)sp * M * N > part_elems) sp = 1;
     const int zl = (ktpp + sp - 1) / sp;
     const int nz = (ktpp + zl - 1) / zl;
-    const double beta_c = (k0 == 0) ? beta : 1.0;
     dim3 grid(d.Np2 / SBN, d.Mp / BM, nz);
     const int tok = kstats_begin(s, K_TC_SLICE, 8.0 * M * N * (double)Kc);
     tc_slice_kernel<<<grid, 576, S_SMEM, s>>>(ma, mb, d.npairs, ktpp, zl, M, N,
