@@ -301,91 +301,6 @@ __global__ void sigma2_kernel(const cplx* __restrict__ G,
   }
 }
 
-// The same as sigma2_kernel, tiled: one CTA per (I, j) and pair of 32 x 32
-// tiles (a-tile ta <= b-tile tb).  G[I][a][j][b] and G[I][b][j][a] of the
-// two tiles are staged in shared memory with coalesced row reads, so the
-// transposed element is read from shared memory; x1[K][a], x1[K][b] and
-// h[K][.][I][j] of the tile's a and b are staged too.  Writes follow the
-// packed pair order (contiguous in b for each a).
-constexpr int ST = 32;
-constexpr int ST_MAXC = 16;  // ncore staged per tile (larger ncore: rows loop)
-__global__ void __launch_bounds__(256)
-    sigma2_tiled_kernel(const cplx* __restrict__ G, const cplx* __restrict__ x2,
-                        const cplx* __restrict__ x1, const cplx* __restrict__ h,
-                        const double* __restrict__ eps, int nc, int nw, int nv,
-                        int ntile, cplx* __restrict__ s2) {
-  __shared__ cplx ga[ST][ST + 1], gb[ST][ST + 1];
-  __shared__ cplx xa[ST_MAXC][ST], xb[ST_MAXC][ST], ha[ST_MAXC][ST], hb[ST_MAXC][ST];
-  const int npt = ntile * (ntile + 1) / 2;
-  const int64_t blk = blockIdx.x;
-  const int tp = (int)(blk % npt);
-  const int64_t ij = blk / npt;  // I * nw + j
-  const int j = (int)(ij % nw), I = (int)(ij / nw);
-  int ta = 0, rem = tp;
-  while (rem >= ntile - ta) {
-    rem -= ntile - ta;
-    ++ta;
-  }
-  const int tb = ta + rem;
-  const int a0 = ta * ST, b0 = tb * ST;
-  const int64_t ldG = (int64_t)nw * nv;  // stride between a rows of one (I, j)
-  const cplx* Gij = G + ((int64_t)I * nv * nw + j) * nv;  // (a, b) -> a ldG + b
-  for (int e = threadIdx.x; e < ST * ST; e += blockDim.x) {
-    const int r = e / ST, c = e % ST;
-    const int a = a0 + r, b = b0 + c;
-    ga[r][c] = (a < nv && b < nv) ? Gij[(int64_t)a * ldG + b] : cmake(0, 0);
-    const int bb = b0 + r, aa = a0 + c;
-    gb[r][c] = (bb < nv && aa < nv) ? Gij[(int64_t)bb * ldG + aa] : cmake(0, 0);
-  }
-  const int o = nc + nw;
-  const int64_t npair = (int64_t)nv * (nv - 1) / 2;
-  const int64_t dbase = ij * npair;
-  const int64_t hs = (int64_t)nv * nc * nw;  // stride of K in h
-  const int64_t hij = (int64_t)I * nw + j;
-  cplx acc_h[4];
-  for (int q = 0; q < 4; ++q) acc_h[q] = cmake(0, 0);
-  // the <Kb||Ij> terms, sum_K x1[K][a] h[K][b] - x1[K][b] h[K][a], in
-  // groups of ST_MAXC cores
-  for (int K0 = 0; h && K0 < nc; K0 += ST_MAXC) {
-    const int kc = min(ST_MAXC, nc - K0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kc * ST; e += blockDim.x) {
-      const int K = e / ST, t = e % ST;
-      const int a = a0 + t, b = b0 + t;
-      xa[K][t] = a < nv ? x1[(int64_t)(K0 + K) * nv + a] : cmake(0, 0);
-      xb[K][t] = b < nv ? x1[(int64_t)(K0 + K) * nv + b] : cmake(0, 0);
-      ha[K][t] = a < nv ? h[(K0 + K) * hs + (int64_t)a * nc * nw + hij] : cmake(0, 0);
-      hb[K][t] = b < nv ? h[(K0 + K) * hs + (int64_t)b * nc * nw + hij] : cmake(0, 0);
-    }
-    __syncthreads();
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + q * blockDim.x;
-      const int r = e / ST, c = e % ST;
-      cplx acc = acc_h[q];
-      for (int K = 0; K < kc; ++K)
-        acc = cadd(acc, csub(cmul(xa[K][r], hb[K][c]), cmul(xb[K][c], ha[K][r])));
-      acc_h[q] = acc;
-    }
-  }
-  __syncthreads();
-  for (int q = 0; q < 4; ++q) {
-    const int e = threadIdx.x + q * blockDim.x;
-    const int r = e / ST, c = e % ST;
-    const int a = a0 + r, b = b0 + c;
-    if (a >= nv || b >= nv || a >= b) continue;
-    const int64_t d = dbase + pair_index(a, b, nv);
-    cplx out = csub(gb[c][r], ga[r][c]);
-    out = cadd(out, acc_h[q]);
-    if (x2) {
-      const cplx x = x2[d];
-      const double m22 = eps[o + a] + eps[o + b] - eps[I] - eps[nc + j];
-      out.x += m22 * x.x;
-      out.y += m22 * x.y;
-    }
-    s2[d] = out;
-  }
-}
-
 // F[I][j][a][b] = -(A[a][b] - A[b][a]) + T[a][b], A and T as [I][j][a][b]
 __global__ void pack_moment_kernel(const cplx* __restrict__ A,
                                    const cplx* __restrict__ T, int nc, int nw,
@@ -518,6 +433,101 @@ struct Ar64 {
 };
 static_assert(sizeof(ArDF::E) == sizeof(cplx) && sizeof(Ar64::E) == sizeof(cplx),
               "staged elements are 16 bytes under both policies");
+
+// The same as sigma2_kernel, tiled: one CTA per (I, j) and pair of 32 x 32
+// tiles (a-tile ta <= b-tile tb).  G[I][a][j][b] and G[I][b][j][a] of the
+// two tiles are staged in shared memory with coalesced row reads, so the
+// transposed element is read from shared memory; x1[K][a], x1[K][b] and
+// h[K][.][I][j] of the tile's a and b are staged too.  Writes follow the
+// packed pair order (contiguous in b for each a).  The <Kb||Ij> terms take
+// 24 complex products per element: P = ArDF runs them in double-float on
+// the FP32 pipes (this GPU's FP64 rate is a small fraction of its FP32
+// rate), P = Ar64 in FP64.
+constexpr int ST = 32;
+constexpr int ST_MAXC = 16;  // ncore staged per tile (larger ncore: rows loop)
+template <class P>
+__global__ void __launch_bounds__(256)
+    sigma2_tiled_kernel(const cplx* __restrict__ G, const cplx* __restrict__ x2,
+                        const cplx* __restrict__ x1, const cplx* __restrict__ h,
+                        const double* __restrict__ eps, int nc, int nw, int nv,
+                        int ntile, cplx* __restrict__ s2) {
+  typedef typename P::E E;
+  __shared__ cplx ga[ST][ST + 1], gb[ST][ST + 1];
+  __shared__ E xa[ST_MAXC][ST], xb[ST_MAXC][ST], ha[ST_MAXC][ST], hb[ST_MAXC][ST];
+  const int npt = ntile * (ntile + 1) / 2;
+  const int64_t blk = blockIdx.x;
+  const int tp = (int)(blk % npt);
+  const int64_t ij = blk / npt;  // I * nw + j
+  const int j = (int)(ij % nw), I = (int)(ij / nw);
+  int ta = 0, rem = tp;
+  while (rem >= ntile - ta) {
+    rem -= ntile - ta;
+    ++ta;
+  }
+  const int tb = ta + rem;
+  const int a0 = ta * ST, b0 = tb * ST;
+  const int64_t ldG = (int64_t)nw * nv;  // stride between a rows of one (I, j)
+  const cplx* Gij = G + ((int64_t)I * nv * nw + j) * nv;  // (a, b) -> a ldG + b
+  for (int e = threadIdx.x; e < ST * ST; e += blockDim.x) {
+    const int r = e / ST, c = e % ST;
+    const int a = a0 + r, b = b0 + c;
+    ga[r][c] = (a < nv && b < nv) ? Gij[(int64_t)a * ldG + b] : cmake(0, 0);
+    const int bb = b0 + r, aa = a0 + c;
+    gb[r][c] = (bb < nv && aa < nv) ? Gij[(int64_t)bb * ldG + aa] : cmake(0, 0);
+  }
+  const int o = nc + nw;
+  const int64_t npair = (int64_t)nv * (nv - 1) / 2;
+  const int64_t dbase = ij * npair;
+  const int64_t hs = (int64_t)nv * nc * nw;  // stride of K in h
+  const int64_t hij = (int64_t)I * nw + j;
+  // sum_K x1[K][a] h[K][b] and sum_K x1[K][b] h[K][a] per element
+  typename P::Acc acc_p[4], acc_m[4];
+  for (int q = 0; q < 4; ++q) {
+    P::zero(acc_p[q]);
+    P::zero(acc_m[q]);
+  }
+  // the <Kb||Ij> terms, sum_K x1[K][a] h[K][b] - x1[K][b] h[K][a], in
+  // groups of ST_MAXC cores
+  for (int K0 = 0; h && K0 < nc; K0 += ST_MAXC) {
+    const int kc = min(ST_MAXC, nc - K0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kc * ST; e += blockDim.x) {
+      const int K = e / ST, t = e % ST;
+      const int a = a0 + t, b = b0 + t;
+      xa[K][t] = P::load(a < nv ? x1[(int64_t)(K0 + K) * nv + a] : cmake(0, 0));
+      xb[K][t] = P::load(b < nv ? x1[(int64_t)(K0 + K) * nv + b] : cmake(0, 0));
+      ha[K][t] = P::load(a < nv ? h[(K0 + K) * hs + (int64_t)a * nc * nw + hij] : cmake(0, 0));
+      hb[K][t] = P::load(b < nv ? h[(K0 + K) * hs + (int64_t)b * nc * nw + hij] : cmake(0, 0));
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      const int e = threadIdx.x + q * blockDim.x;
+      const int r = e / ST, c = e % ST;
+      for (int K = 0; K < kc; ++K) {
+        P::mac(acc_p[q], xa[K][r], hb[K][c]);
+        P::mac(acc_m[q], xb[K][c], ha[K][r]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = 0; q < 4; ++q) {
+    const int e = threadIdx.x + q * blockDim.x;
+    const int r = e / ST, c = e % ST;
+    const int a = a0 + r, b = b0 + c;
+    if (a >= nv || b >= nv || a >= b) continue;
+    const int64_t d = dbase + pair_index(a, b, nv);
+    cplx out = csub(gb[c][r], ga[r][c]);
+    if (h) out = cadd(out, csub(P::value(acc_p[q]), P::value(acc_m[q])));
+    if (x2) {
+      const cplx x = x2[d];
+      const double m22 = eps[o + a] + eps[o + b] - eps[I] - eps[nc + j];
+      out.x += m22 * x.x;
+      out.y += m22 * x.y;
+    }
+    s2[d] = out;
+  }
+}
+
 
 constexpr int TSN = 16;  // n-tile of ts_dot
 
@@ -1045,12 +1055,16 @@ void h_conj_transpose(cudaStream_t s, const cplx* h, int nc, int nw, int nv,
 
 void sigma2_finish(cudaStream_t s, const cplx* G, const cplx* x2,
                    const cplx* x1, const cplx* h, const double* eps, int ncore,
-                   int nval, int nvirt, cplx* s2) {
+                   int nval, int nvirt, cplx* s2, bool fp64) {
   const int nt = (nvirt + ST - 1) / ST;
   const int64_t nblk = (int64_t)ncore * nval * (nt * (nt + 1) / 2);
   CVS_REQUIRE(nblk < (1LL << 31), -1, "sigma2_finish: too many tiles");
-  sigma2_tiled_kernel<<<(unsigned)nblk, 256, 0, s>>>(G, x2, x1, h, eps, ncore, nval, nvirt,
-                                                     nt, s2);
+  if (fp64)
+    sigma2_tiled_kernel<Ar64><<<(unsigned)nblk, 256, 0, s>>>(G, x2, x1, h, eps, ncore, nval,
+                                                             nvirt, nt, s2);
+  else
+    sigma2_tiled_kernel<ArDF><<<(unsigned)nblk, 256, 0, s>>>(G, x2, x1, h, eps, ncore, nval,
+                                                             nvirt, nt, s2);
   CVS_CHECK_LAUNCH();
 }
 

@@ -246,6 +246,63 @@ __global__ void splitk_reduce_kernel(int M, int N, int nz, const cplx* part,
     *d = cmake(sr, si);
   }
 }
+// C = alpha A B + beta C for a few columns (N <= GEMV_MAXN) when A's rows
+// are contiguous along k: a warp per row of A, lanes along k, the N sums in
+// registers; B's N columns are re-read from L2 by every row.
+constexpr int GEMV_MAXN = 8;
+__global__ void __launch_bounds__(256)
+    zgemv_rows_kernel(int M, int N, int K, double alpha, View A, View B, double beta,
+                      View C) {
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t m = warp; m < M; m += nwarp) {
+    const cplx* a = A.p + vrow(A, m);
+    double re[GEMV_MAXN], im[GEMV_MAXN];
+#pragma unroll
+    for (int q = 0; q < GEMV_MAXN; ++q) re[q] = im[q] = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      cplx x = a[k];
+      if (A.conj) x.y = -x.y;
+      const int64_t bo = vrow(B, k);
+#pragma unroll
+      for (int q = 0; q < GEMV_MAXN; ++q) {
+        if (q < N) {
+          cplx y = B.p[bo + vcol(B, q)];
+          if (B.conj) y.y = -y.y;
+          re[q] = fma(x.x, y.x, fma(-x.y, y.y, re[q]));
+          im[q] = fma(x.x, y.y, fma(x.y, y.x, im[q]));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < GEMV_MAXN; ++q) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
+        im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
+      }
+    }
+    if (lane < N) {
+      double r = 0.0, i = 0.0;
+#pragma unroll
+      for (int q = 0; q < GEMV_MAXN; ++q)
+        if (q == lane) {
+          r = re[q];
+          i = im[q];
+        }
+      cplx* d = C.p + vrow(C, m) + vcol(C, lane);
+      cplx o = cmake(alpha * r, alpha * i);
+      if (beta != 0.0) {
+        const cplx old = *d;
+        o.x += beta * old.x;
+        o.y += beta * old.y;
+      }
+      *d = o;
+    }
+  }
+}
+
 }  // namespace
 
 void splitk_reduce(cudaStream_t s, int M, int N, int nz, const cplx* part,
@@ -280,6 +337,15 @@ void zgemm_f64(cudaStream_t s, int M, int N, int K, double alpha, View A,
   if (K <= 0) {
     // C = beta * C
     scale_view(s, M, N, beta, C, batch);
+    return;
+  }
+  if (batch == 1 && N <= GEMV_MAXN && A.cs_lo == 1 && A.c_lo == INT32_MAX &&
+      (int64_t)M * K >= (1 << 20) && M >= 8 * 152) {
+    const int tok = kstats_begin(s, K_F64_GEMM, 8.0 * M * N * (double)K);
+    zgemv_rows_kernel<<<grid1d((int64_t)M * 32, 256), 256, 0, s>>>(M, N, K, alpha, A, B,
+                                                                   beta, C);
+    CVS_CHECK_LAUNCH();
+    kstats_end(s, tok);
     return;
   }
   if (batch == 1 && part && smallmn_ok(M, N, K)) {

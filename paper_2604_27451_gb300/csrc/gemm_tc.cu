@@ -582,7 +582,8 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
 __global__ void __launch_bounds__(576, 1)
     tc_slice_kernel(const __grid_constant__ CUtensorMap tmA,
                     const __grid_constant__ CUtensorMap tmB, int npairs,
-                    int ktpp, int zl, int M, int N, const int* __restrict__ eA,
+                    int ktpp, int kpb, int kb_off, int zl, int M, int N,
+                    const int* __restrict__ eA,
                     const int* __restrict__ eB, double alpha, double beta,
                     View C, cplx* part, int* err) {
   extern __shared__ uint8_t smem_raw[];
@@ -636,7 +637,11 @@ __global__ void __launch_bounds__(576, 1)
     // TMA producer over this CTA's k-tiles of every pair
     const int nkt = npairs * zlen;
     for (int i = 0; i < nkt; ++i) {
-      const int kt = (i / zlen) * ktpp + zb + i % zlen;
+      const int p = i / zlen, t = zb + i % zlen;  // pair, k-tile within it
+      const int kt = p * ktpp + t;
+      // B: segment 2 p + (re / im half), K block kb_off + (t mod Kp / BK)
+      const int hk = ktpp >> 1;
+      const int xb = (2 * p + t / hk) * kpb + (kb_off + t % hk) * BK;
       const int s = i % SSTAGES;
       const uint32_t ph = (i / SSTAGES) & 1;
       if (i >= SSTAGES && !mbar_wait(&empty[s], ph ^ 1)) {
@@ -646,7 +651,7 @@ __global__ void __launch_bounds__(576, 1)
       if (fail) break;
       mbar_expect_tx(&full[s], S_STAGE);
       tma_load(&tmA, &full[s], sA + s * S_A_TILE, kt * BK, m0);
-      tma_load(&tmB, &full[s], sB + s * S_B_TILE, kt * BK, n0);
+      tma_load(&tmB, &full[s], sB + s * S_B_TILE, xb, n0);
     }
   } else if (threadIdx.x == 32) {
     // MMA issuer: one exact run per (pair, run) into alternating buffers
@@ -768,43 +773,58 @@ __device__ __forceinline__ int64_t vcol32(const View& v, int c) {
   return (int64_t)h * v.cs_hi + (int64_t)(c - h * v.c_lo) * v.cs_lo;
 }
 
-// per-row (A: rows m, max over k) exponent e with max |re|, |im| < 2^e (0
-// for an all-zero row); one warp per row
+// Exponents over [k0, k0 + K): e with max |re|, |im| < 2^e for every
+// element of a row of A (row_exp) or a column of B (col_exp); an all-zero
+// line gets -1022.  A warp takes one (line, K segment of EXP_SEG) task and
+// folds its maximum into e[] with atomicMax, so an operand with few lines
+// and a K in the millions still spreads over every SM; the caller presets
+// e[] below -1022 (bytes 0x80).
+constexpr int EXP_SEG = 4096;
 __global__ void row_exp_kernel(View A, int M, int K, int k0, int* e) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nwarp = (gridDim.x * blockDim.x) >> 5;
-  for (int m = warp; m < M; m += nwarp) {
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nsg = (K + EXP_SEG - 1) / EXP_SEG;
+  const int64_t ntask = (int64_t)M * nsg;
+  for (int64_t t = warp; t < ntask; t += nwarp) {
+    const int m = (int)(t / nsg), k1 = (int)(t % nsg) * EXP_SEG;
+    const int k2 = min(K, k1 + EXP_SEG);
     const int64_t ro = vrow(A, m);
     int mx = 0;
-    for (int k = lane; k < K; k += 32) {
+    for (int k = k1 + lane; k < k2; k += 32) {
       const cplx a = A.p[ro + vcol32(A, k0 + k)];
       mx = max(mx, max(exp_field(a.x), exp_field(a.y)));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) e[m] = mx > 0 ? mx - 1022 : 0;
+    if (lane == 0) atomicMax(e + m, mx - 1022);
   }
 }
 
-// per-column (B: columns n, max over k) exponent
 __global__ void col_exp_kernel(View B, int K, int k0, int N, int* e) {
-  for (int n = blockIdx.x; n < N; n += gridDim.x) {
-    int mx = 0;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nsg = (K + EXP_SEG - 1) / EXP_SEG;
+  const int64_t ntask = (int64_t)N * nsg;
+  for (int64_t t = warp; t < ntask; t += nwarp) {
+    const int n = (int)(t / nsg), k1 = (int)(t % nsg) * EXP_SEG;
+    const int k2 = min(K, k1 + EXP_SEG);
     const int64_t co = vcol(B, n);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    int mx = 0;
+    for (int k = k1 + lane; k < k2; k += 32) {
       const cplx b = B.p[vrow(B, k0 + k) + co];
       mx = max(mx, max(exp_field(b.x), exp_field(b.y)));
     }
-    __shared__ int red[256];
-    red[threadIdx.x] = mx;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] = max(red[threadIdx.x], red[threadIdx.x + o]);
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) e[n] = red[0] > 0 ? red[0] - 1022 : 0;
-    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) atomicMax(e + n, mx - 1022);
   }
+}
+
+unsigned warp_tasks_grid(int64_t lines, int K, int seg) {
+  const int64_t ntask = lines * ((K + seg - 1) / seg);
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((ntask + 7) / 8, 152 * 32));
 }
 
 // S balanced 7-bit slices of t = x 2^-e (|t| < 1): T = round(t 2^(7S))
@@ -835,32 +855,52 @@ __device__ __forceinline__ void slices(double x, int e, __nv_bfloat16* q) {
   q[0] = __float2bfloat16_rn((float)T);
 }
 
-// A' [Mp][2 npairs Kp]: row m, segment 2p + {0: re, 1: im} of slice c_si[p];
-// one warp per row, lanes along k
+// A' [Mp][2 npairs Kp]: row m, segment 2p + {0: re, 1: im} of slice c_si[p].
+// A warp takes one (row, K segment of PACK_SEG) task; a lane packs two
+// adjacent k into bf16 pairs (4-byte stores).
+constexpr int PACK_SEG = 2048;
+__device__ __forceinline__ void ld_pair(const View& A, int64_t ro, bool live, int K,
+                                        int k0, int k, cplx& a0, cplx& a1) {
+  a0 = a1 = cmake(0, 0);
+  if (!live) return;
+  if (k < K) a0 = A.p[ro + vcol32(A, k0 + k)];
+  if (k + 1 < K) a1 = A.p[ro + vcol32(A, k0 + k + 1)];
+  if (A.conj) {
+    a0.y = -a0.y;
+    a1.y = -a1.y;
+  }
+}
+
 template <int S>
 __global__ void slice_pack_a(View A, int M, int K, int k0, int Mp, int Kp,
                              int npairs, const int* __restrict__ eA,
                              __nv_bfloat16* out) {
   const int64_t ld = (int64_t)2 * npairs * Kp;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nwarp = (gridDim.x * blockDim.x) >> 5;
-  for (int m = warp; m < Mp; m += nwarp) {
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nsg = (Kp + PACK_SEG - 1) / PACK_SEG;
+  const int64_t ntask = (int64_t)Mp * nsg;
+  for (int64_t t = warp; t < ntask; t += nwarp) {
+    const int m = (int)(t / nsg), k1 = (int)(t % nsg) * PACK_SEG;
+    const int k2 = min(Kp, k1 + PACK_SEG);
     const bool live = m < M;
     const int64_t ro = live ? vrow(A, m) : 0;
     const int e = live ? eA[m] : 0;
     __nv_bfloat16* o = out + (int64_t)m * ld;
-    for (int k = lane; k < Kp; k += 32) {
-      cplx a = cmake(0, 0);
-      if (live && k < K) {
-        a = A.p[ro + vcol32(A, k0 + k)];
-        if (A.conj) a.y = -a.y;
-      }
-      __nv_bfloat16 re[S], im[S];
-      slices<S>(a.x, e, re);
-      slices<S>(a.y, e, im);
+    for (int k = k1 + 2 * lane; k < k2; k += 64) {
+      cplx a0, a1;
+      ld_pair(A, ro, live, K, k0, k, a0, a1);
+      __nv_bfloat16 r0[S], i0[S], r1[S], i1[S];
+      slices<S>(a0.x, e, r0);
+      slices<S>(a0.y, e, i0);
+      slices<S>(a1.x, e, r1);
+      slices<S>(a1.y, e, i1);
       for (int p = 0; p < npairs; ++p) {
-        o[(2 * p) * (int64_t)Kp + k] = re[c_si[p]];
-        o[(2 * p + 1) * (int64_t)Kp + k] = im[c_si[p]];
+        const int q = c_si[p];
+        *(__nv_bfloat162*)(o + (2 * p) * (int64_t)Kp + k) = __halves2bfloat162(r0[q], r1[q]);
+        *(__nv_bfloat162*)(o + (2 * p + 1) * (int64_t)Kp + k) =
+            __halves2bfloat162(i0[q], i1[q]);
       }
     }
   }
@@ -928,8 +968,9 @@ constexpr int R_RUN = 4;                 // units (K block, part) per exact run
 
 __global__ void __launch_bounds__(576, 1)
     tc_slice4r_kernel(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, int Kp, int nkb,
-                      int zl, int M, int N, const int* __restrict__ eA,
+                      const __grid_constant__ CUtensorMap tmB, int Kp, int kpb,
+                      int kb_off, int nkb, int zl, int M, int N,
+                      const int* __restrict__ eA,
                       const int* __restrict__ eB, double alpha, double beta,
                       View C, cplx* part, int* err) {
   extern __shared__ uint8_t smem_raw[];
@@ -995,7 +1036,7 @@ __global__ void __launch_bounds__(576, 1)
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         tma_load(&tmB, &full[s], st + 4 * R_A_TILE + j * R_B_TILE,
-                 (2 * j + c) * Kp + kb * BK, n0);
+                 (2 * j + c) * kpb + (kb_off + kb) * BK, n0);
     }
   } else if (threadIdx.x == 32) {
     // MMA issuer: for each unit, the ten pairs into their order's
@@ -1102,30 +1143,35 @@ __global__ void __launch_bounds__(576, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// A'' [Mp][8 Kp]: segment 2 i + {0: re, 1: im} holds slice i
+// A'' [Mp][8 Kp]: segment 2 i + {0: re, 1: im} holds slice i; tasks as in
+// slice_pack_a
 __global__ void slice4r_pack_a(View A, int M, int K, int k0, int Mp, int Kp,
                                const int* __restrict__ eA, __nv_bfloat16* out) {
   const int64_t ld = (int64_t)8 * Kp;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int nwarp = (gridDim.x * blockDim.x) >> 5;
-  for (int m = warp; m < Mp; m += nwarp) {
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int nsg = (Kp + PACK_SEG - 1) / PACK_SEG;
+  const int64_t ntask = (int64_t)Mp * nsg;
+  for (int64_t t = warp; t < ntask; t += nwarp) {
+    const int m = (int)(t / nsg), k1 = (int)(t % nsg) * PACK_SEG;
+    const int k2 = min(Kp, k1 + PACK_SEG);
     const bool live = m < M;
     const int64_t ro = live ? vrow(A, m) : 0;
     const int e = live ? eA[m] : 0;
     __nv_bfloat16* o = out + (int64_t)m * ld;
-    for (int k = lane; k < Kp; k += 32) {
-      cplx a = cmake(0, 0);
-      if (live && k < K) {
-        a = A.p[ro + vcol32(A, k0 + k)];
-        if (A.conj) a.y = -a.y;
-      }
-      __nv_bfloat16 re[4], im[4];
-      slices<4>(a.x, e, re);
-      slices<4>(a.y, e, im);
+    for (int k = k1 + 2 * lane; k < k2; k += 64) {
+      cplx a0, a1;
+      ld_pair(A, ro, live, K, k0, k, a0, a1);
+      __nv_bfloat16 r0[4], i0[4], r1[4], i1[4];
+      slices<4>(a0.x, e, r0);
+      slices<4>(a0.y, e, i0);
+      slices<4>(a1.x, e, r1);
+      slices<4>(a1.y, e, i1);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        o[(2 * i) * (int64_t)Kp + k] = re[i];
-        o[(2 * i + 1) * (int64_t)Kp + k] = im[i];
+        *(__nv_bfloat162*)(o + (2 * i) * (int64_t)Kp + k) = __halves2bfloat162(r0[i], r1[i]);
+        *(__nv_bfloat162*)(o + (2 * i + 1) * (int64_t)Kp + k) = __halves2bfloat162(i0[i], i1[i]);
       }
     }
   }
@@ -1165,43 +1211,51 @@ __global__ void slice4r_pack_b(View B, int K, int k0, int N, int Np2, int Kp,
 
 // packed geometry: SLICE4 packs each slice once (8 segments, N' tiles of
 // 64, the slice-reuse kernel); SLICE7 packs one segment pair per slice pair
-// (56 segments, N' tiles of 128)
+// (56 segments, N' tiles of 128).  K runs in chunks of kc so that the packs
+// of a chunk stay within PACK_BUDGET; a B operand held in a cache is packed
+// once over its whole K (KpF) and only A's pack counts against the budget.
 struct SDims {
-  int Mp, Np2, npairs, nseg, kc;
+  int Mp, Np2, npairs, nseg, kc, KpF;
   size_t a_bytes, b_bytes, e_bytes;
 };
-SDims sdims_of(int M, int N, int K, int nslices) {
+SDims sdims_of(int M, int N, int K, int nslices, bool b_cached) {
   SDims d;
   const int tn = nslices == 4 ? RBN : SBN;
   d.Mp = (M + BM - 1) / BM * BM;
   d.Np2 = (2 * N + tn - 1) / tn * tn;
   d.npairs = nslices * (nslices + 1) / 2;
   d.nseg = nslices == 4 ? 8 : 2 * d.npairs;
-  const size_t per_k = (size_t)(d.Mp + d.Np2) * d.nseg * 2;
+  d.KpF = (int)(((int64_t)K + BK - 1) / BK * BK);
+  const size_t per_k = (size_t)(d.Mp + (b_cached ? 0 : d.Np2)) * d.nseg * 2;
   int64_t kc = (int64_t)(PACK_BUDGET / per_k) / BK * BK;
   kc = std::max<int64_t>(kc, BK);
-  d.kc = (int)std::min<int64_t>(kc, ((int64_t)K + BK - 1) / BK * BK);
+  d.kc = (int)std::min<int64_t>(kc, d.KpF);
   d.a_bytes = (size_t)d.Mp * d.nseg * d.kc * 2;
-  d.b_bytes = (size_t)d.Np2 * d.nseg * d.kc * 2;
+  d.b_bytes = b_cached ? 0 : (size_t)d.Np2 * d.nseg * d.kc * 2;
   d.e_bytes = ((size_t)d.Mp + d.Np2 / 2 + 64) * sizeof(int);
   return d;
 }
 
-
 }  // namespace
 
-size_t slice_workspace_bytes(int M, int N, int K, int nslices) {
-  SDims d = sdims_of(M, N, K, nslices);
+size_t slice_workspace_bytes(int M, int N, int K, int nslices, bool b_cached) {
+  SDims d = sdims_of(M, N, K, nslices, b_cached);
   return d.a_bytes + d.b_bytes + d.e_bytes + 256;
 }
 
-size_t slice_bcache_bytes(int M, int N, int K, int nslices, int* kc,
-                          size_t* a_bytes) {
-  SDims d = sdims_of(M, N, K, nslices);
-  const int64_t nch = ((int64_t)K + d.kc - 1) / d.kc;
-  if (kc) *kc = d.kc;
-  if (a_bytes) *a_bytes = d.a_bytes;
-  return (size_t)nch * (d.b_bytes + ((size_t)d.Np2 / 2 + 64) * sizeof(int)) + 256;
+size_t slice_bcache_bytes(int N, int K, int nslices) {
+  SDims d = sdims_of(1, N, K, nslices, true);
+  return (size_t)d.Np2 * d.nseg * d.KpF * 2 + ((size_t)d.Np2 / 2 + 64) * sizeof(int) + 256;
+}
+
+int64_t slice_row_slab(int M, int N, int K, int nslices) {
+  SDims d = sdims_of(M, N, K, nslices, false);
+  if (d.kc >= d.KpF) return M;  // K is whole already
+  const size_t per_row = (size_t)d.nseg * d.KpF * 2;
+  const size_t bfull = (size_t)d.Np2 * d.nseg * d.KpF * 2;
+  if (bfull >= PACK_BUDGET / 2) return M;
+  const int64_t rows = (int64_t)((PACK_BUDGET - bfull) / per_row) / BM * BM;
+  return rows >= 16 * BM ? rows : M;
 }
 
 void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
@@ -1210,7 +1264,7 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
                  SliceBCache* bc) {
   if (M <= 0 || N <= 0) return;
   CVS_REQUIRE(nslices == 4 || nslices == 7, -1, "zgemm_slice: 4 or 7 slices");
-  SDims d = sdims_of(M, N, K, nslices);
+  SDims d = sdims_of(M, N, K, nslices, bc != nullptr);
   CVS_REQUIRE(work_bytes >= d.a_bytes + d.b_bytes + d.e_bytes, -1,
               "zgemm_slice: workspace too small");
   static std::once_flag attr;
@@ -1226,48 +1280,65 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
   int* eB = eA + d.Mp;
   const bool reuse = nslices == 4;
   const int64_t tiles = (int64_t)(d.Np2 / (reuse ? RBN : SBN)) * (d.Mp / BM);
-  const int64_t nch = ((int64_t)K + d.kc - 1) / d.kc;
   const size_t eb_n = (size_t)d.Np2 / 2 + 64;
-  CVS_REQUIRE(!bc || bc->bytes >= (size_t)nch * (d.b_bytes + eb_n * sizeof(int)),
-              -1, "zgemm_slice: B cache too small");
+  const size_t bfull = (size_t)d.Np2 * d.nseg * d.KpF * 2;
+  if (bc) {
+    // the cached B: packed once over the whole K, with whole-column exponents
+    CVS_REQUIRE(bc->bytes >= bfull + eb_n * sizeof(int), -1, "zgemm_slice: B cache too small");
+    if (!bc->filled) {
+      int* ec = (int*)((char*)bc->base + bfull);
+      __nv_bfloat16* bq = (__nv_bfloat16*)bc->base;
+      CVS_CUDA(cudaMemsetAsync(ec, 0x80, eb_n * sizeof(int), s));
+      col_exp_kernel<<<warp_tasks_grid(N, K, EXP_SEG), 256, 0, s>>>(B, K, 0, N, ec);
+      CVS_CHECK_LAUNCH();
+      const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * d.KpF, 256);
+      if (reuse)
+        slice4r_pack_b<<<gb, 256, 0, s>>>(B, K, 0, N, d.Np2, d.KpF, ec, bq);
+      else
+        slice_pack_b<7><<<gb, 256, 0, s>>>(B, K, 0, N, d.Np2, d.KpF, d.npairs, ec, bq);
+      CVS_CHECK_LAUNCH();
+      bc->filled = true;
+    }
+  }
   for (int k0 = 0; k0 < K; k0 += d.kc) {
     const int Kc = std::min(d.kc, K - k0);
     const int Kp = (Kc + BK - 1) / BK * BK;
-    const int64_t ci = k0 / d.kc;
-    // B's packed slices and exponents: this chunk's slot of the cache, or
+    // B's packed slices and exponents: the cache (whole K; this chunk starts
+    // at K block k0 / BK of each segment of KpF) or this chunk's packs in
     // the workspace
-    __nv_bfloat16* bpc = bc ? (__nv_bfloat16*)((char*)bc->base + ci * d.b_bytes) : bp;
-    int* eBc = bc ? (int*)((char*)bc->base + nch * d.b_bytes) + ci * eb_n : eB;
-    const bool pack_b = !bc || !bc->filled;
-    row_exp_kernel<<<(unsigned)std::min<int64_t>((M + 7) / 8, 152 * 32), 256, 0, s>>>(
-        A, M, Kc, k0, eA);
+    const __nv_bfloat16* bpc = bc ? (const __nv_bfloat16*)bc->base : bp;
+    const int* eBc = bc ? (const int*)((const char*)bc->base + bfull) : eB;
+    const int kpb = bc ? d.KpF : Kp, kb_off = bc ? k0 / BK : 0;
+    CVS_CUDA(cudaMemsetAsync(eA, 0x80, (size_t)d.Mp * sizeof(int), s));
+    row_exp_kernel<<<warp_tasks_grid(M, Kc, EXP_SEG), 256, 0, s>>>(A, M, Kc, k0, eA);
     CVS_CHECK_LAUNCH();
-    if (pack_b) {
-      col_exp_kernel<<<std::min(N, 152 * 16), 256, 0, s>>>(B, Kc, k0, N, eBc);
+    if (!bc) {
+      CVS_CUDA(cudaMemsetAsync(eB, 0x80, eb_n * sizeof(int), s));
+      col_exp_kernel<<<warp_tasks_grid(N, Kc, EXP_SEG), 256, 0, s>>>(B, Kc, k0, N, eB);
       CVS_CHECK_LAUNCH();
     }
-    const unsigned ga = (unsigned)std::min<int64_t>((d.Mp + 7) / 8, 152 * 32);
+    const unsigned ga = warp_tasks_grid(d.Mp, Kp, PACK_SEG);
     const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * Kp, 256);
     if (reuse) {
       slice4r_pack_a<<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, eA, ap);
       CVS_CHECK_LAUNCH();
-      if (pack_b) {
-        slice4r_pack_b<<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, eBc, bpc);
+      if (!bc) {
+        slice4r_pack_b<<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, eB, bp);
         CVS_CHECK_LAUNCH();
       }
     } else {
       slice_pack_a<7><<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, d.npairs, eA, ap);
       CVS_CHECK_LAUNCH();
-      if (pack_b) {
-        slice_pack_b<7><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eBc, bpc);
+      if (!bc) {
+        slice_pack_b<7><<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, d.npairs, eB, bp);
         CVS_CHECK_LAUNCH();
       }
     }
-    const int64_t kcols = (int64_t)d.nseg * Kp;
+    const int64_t kcols = (int64_t)d.nseg * Kp, kcols_b = (int64_t)d.nseg * kpb;
     const double beta_c = (k0 == 0) ? beta : 1.0;
     if (reuse) {
       CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
-      CUtensorMap mb = make_map(bpc, d.Np2, kcols, RBN);
+      CUtensorMap mb = make_map(bpc, d.Np2, kcols_b, RBN);
       const int nkb = Kp / BK;  // K blocks; a run spans two
       int sp = tc_splits(tiles, nkb, 2 * (R_RUN / 2));
       if (part == nullptr || (size_t)sp * M * N > part_elems) sp = 1;
@@ -1275,15 +1346,16 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
       const int nz = (nkb + zl - 1) / zl;
       dim3 grid(d.Np2 / RBN, d.Mp / BM, nz);
       const int tok = kstats_begin(s, K_TC_SLICE, 8.0 * M * N * (double)Kc);
-      tc_slice4r_kernel<<<grid, 576, R_SMEM, s>>>(ma, mb, Kp, nkb, zl, M, N, eA, eBc, alpha,
-                                                  beta_c, C, nz > 1 ? part : nullptr, err);
+      tc_slice4r_kernel<<<grid, 576, R_SMEM, s>>>(ma, mb, Kp, kpb, kb_off, nkb, zl, M, N, eA,
+                                                  eBc, alpha, beta_c, C,
+                                                  nz > 1 ? part : nullptr, err);
       CVS_CHECK_LAUNCH();
       kstats_end(s, tok);
       if (nz > 1) splitk_reduce(s, M, N, nz, part, beta_c, C);
       continue;
     }
     CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
-    CUtensorMap mb = make_map(bpc, d.Np2, kcols, SBN);
+    CUtensorMap mb = make_map(bpc, d.Np2, kcols_b, SBN);
     const int ktpp = 2 * Kp / BK;
     int sp = tc_splits(tiles, ktpp, RUN_KT);
     if (part == nullptr || (size_t)sp * M * N > part_elems) sp = 1;
@@ -1291,14 +1363,13 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
     const int nz = (ktpp + zl - 1) / zl;
     dim3 grid(d.Np2 / SBN, d.Mp / BM, nz);
     const int tok = kstats_begin(s, K_TC_SLICE, 8.0 * M * N * (double)Kc);
-    tc_slice_kernel<<<grid, 576, S_SMEM, s>>>(ma, mb, d.npairs, ktpp, zl, M, N,
+    tc_slice_kernel<<<grid, 576, S_SMEM, s>>>(ma, mb, d.npairs, ktpp, kpb, kb_off, zl, M, N,
                                               eA, eBc, alpha, beta_c, C,
                                               nz > 1 ? part : nullptr, err);
     CVS_CHECK_LAUNCH();
     kstats_end(s, tok);
     if (nz > 1) splitk_reduce(s, M, N, nz, part, beta_c, C);
   }
-  if (bc) bc->filled = true;
 }
 
 }  // namespace cvs

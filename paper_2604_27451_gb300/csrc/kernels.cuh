@@ -30,17 +30,20 @@ bool tc_available();
 // Exact-accumulation slice GEMM on the tensor cores (see gemm_tc.cu):
 // nslices = 4 (10 slice products, ~2^-28 of row max x column max) or 7
 // (28 products, FP64 class).
-size_t slice_workspace_bytes(int M, int N, int K, int nslices);
+// workspace of one call (b_cached: B comes from a SliceBCache)
+size_t slice_workspace_bytes(int M, int N, int K, int nslices, bool b_cached = false);
 // Packed slices (and column exponents) of a B operand that does not change
-// between calls, for every K chunk; filled by the first call that gets it.
+// between calls, over its whole K; filled by the first call that gets it.
 struct SliceBCache {
   void* base = nullptr;
   size_t bytes = 0;
   bool filled = false;
 };
-// bytes such a cache needs for this product (and the K chunk used)
-size_t slice_bcache_bytes(int M, int N, int K, int nslices, int* kc,
-                          size_t* a_bytes);
+// bytes such a cache needs for a K x N operand (independent of M)
+size_t slice_bcache_bytes(int N, int K, int nslices);
+// rows per slab when a tall product is better split over M with K whole
+// (its A packs dominate and K would otherwise run in chunks); M when not
+int64_t slice_row_slab(int M, int N, int K, int nslices);
 void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
                  double alpha, View A, View B, double beta, View C, void* work,
                  size_t work_bytes, cplx* part, size_t part_elems, int* err, SliceBCache* bc = nullptr);
@@ -86,10 +89,11 @@ void m11_assemble(cudaStream_t s, int ncore, int nvirt, int o,
 // Yt[I][a][j][b] = antisymmetric unpack of packed doubles x2.
 void unpack_doubles(cudaStream_t s, const cplx* x2, int ncore, int nval,
                     int nvirt, cplx* Yt);
-// sigma2[d] = -(G[I,a,j,b] - G[I,b,j,a]) + (e_a+e_b-e_I-e_j) x2[d]
+// sigma2[d] = -(G[I,a,j,b] - G[I,b,j,a]) + (e_a+e_b-e_I-e_j) x2[d] plus the
+// <Kb||Ij> terms of x1 (h != NULL): in FP64 (fp64) or double-float
 void sigma2_finish(cudaStream_t s, const cplx* G, const cplx* x2,
                    const cplx* x1, const cplx* h, const double* eps, int ncore,
-                   int nval, int nvirt, cplx* s2);
+                   int nval, int nvirt, cplx* s2, bool fp64);
 void h_conj_transpose(cudaStream_t s, const cplx* h, int nc, int nw, int nv,
                       cplx* hT);
 // pack an antisymmetric-by-construction full tensor F[I][j][a][b] with

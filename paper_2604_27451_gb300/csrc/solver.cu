@@ -32,6 +32,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <numeric>
 #include <mutex>
 #include <array>
 #include <complex>
@@ -190,7 +191,7 @@ struct cvsadc_ctx {
     DBuf buf;
     SliceBCache sc;
   };
-  std::map<std::array<int64_t, 12>, std::unique_ptr<BEntry>> bcache;
+  std::map<std::array<int64_t, 11>, std::unique_ptr<BEntry>> bcache;
   size_t bcache_bytes = 0;
   void clear_bcache() {
     bcache.clear();
@@ -236,22 +237,19 @@ bool needs_refine(int p) {
 }
 
 // --------------------------------------------------------------- GEMM hub
-// A cache slot for the packed slices of B when B is a view of the prepared
-// B^P (it does not change between calls), its packs dwarf those of A (so
-// the K chunking does not depend on the number of trial vectors), and the
-// cache stays within min(25 % of free memory, 48 GB); else NULL.
+// A cache slot for the packed slices of B (whole K) when the caller asks for
+// one (a product repeated on every sigma), B is a view of the prepared B^P
+// (it does not change between calls) and the cache stays within min(25 %
+// of free memory, 48 GB); else NULL.
 constexpr double BCACHE_MAX = 48e9;
-SliceBCache* b_cache(cvsadc_ctx* c, int ns, int M, int N, int K, const View& B) {
+SliceBCache* b_cache(cvsadc_ctx* c, int ns, int N, int K, const View& B) {
   if (!c->B.p) return nullptr;
   const cplx* b0 = c->B.c();
   const size_t nb = c->B.bytes / sizeof(cplx);
   if (!b0 || B.p < b0 || B.p >= b0 + nb) return nullptr;
-  int kc = 0;
-  size_t a_bytes = 0;
-  const size_t bytes = slice_bcache_bytes(M, N, K, ns, &kc, &a_bytes);
-  if (bytes < 4 * a_bytes) return nullptr;
-  const std::array<int64_t, 12> key = {(int64_t)(B.p - b0), B.rs_hi, B.rs_lo, B.r_lo,
-                                       B.cs_hi, B.cs_lo, B.c_lo, B.conj, N, K, ns, kc};
+  const size_t bytes = slice_bcache_bytes(N, K, ns);
+  const std::array<int64_t, 11> key = {(int64_t)(B.p - b0), B.rs_hi, B.rs_lo, B.r_lo,
+                                       B.cs_hi, B.cs_lo, B.c_lo, B.conj, N, K, ns};
   auto it = c->bcache.find(key);
   if (it != c->bcache.end()) return &it->second->sc;
   size_t free_b = 0, total_b = 0;
@@ -273,8 +271,21 @@ SliceBCache* b_cache(cvsadc_ctx* c, int ns, int M, int N, int K, const View& B) 
 }
 
 
+// the view from row m0 on (m0 a multiple of its inner row extent when the
+// rows are two-level)
+View rows_from(View v, int64_t m0) {
+  const int64_t off = v.r_lo == INT32_MAX
+                          ? m0 * v.rs_lo
+                          : (m0 / v.r_lo) * v.rs_hi + (m0 % v.r_lo) * v.rs_lo;
+  v.p += off;
+  if (v.ext >= 0) v.ext -= off;
+  return v;
+}
+
+// cache_b: B is the same view of B^P on every call (the sigma products), so
+// its packed slices may be kept
 void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
-          View B, double beta, View C, int batch = 1) {
+          View B, double beta, View C, int batch = 1, bool cache_b = false) {
   A = checked(A);
   B = checked(B);
   C = checked(C);
@@ -291,7 +302,29 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
     CVS_REQUIRE(tc_available(), CVSADC_EINVAL,
                 "tensor-core precisions need an sm_103 GPU with tcgen05");
     const int ns = prec == CVSADC_MIXED_SLICE4 ? 4 : prec == CVSADC_FP64_SLICE7 ? 7 : 0;
-    size_t need = ns ? slice_workspace_bytes(M, N, K, ns) : tc_workspace_bytes(M, N, K, 3);
+    SliceBCache* bc = (ns && batch == 1 && cache_b) ? b_cache(c, ns, N, K, B) : nullptr;
+    if (ns && batch == 1 && !bc) {
+      // a tall product whose A packs dominate: slabs of rows with K whole
+      // (slab boundaries on the inner row extents of A and C)
+      int64_t slab = slice_row_slab(M, N, K, ns);
+      int64_t q = 1;
+      if (A.r_lo < M) q = A.r_lo;
+      if (C.r_lo < M) q = std::lcm(q, (int64_t)C.r_lo);
+      slab = slab / q * q;
+      if (slab > 0 && slab < M) {
+        const size_t need = slice_workspace_bytes((int)slab, N, K, ns);
+        c->s_tc.ensure(need);
+        for (int64_t m0 = 0; m0 < M; m0 += slab) {
+          const int Mi = (int)std::min<int64_t>(slab, M - m0);
+          zgemm_slice(c->stream, ns, Mi, N, K, alpha, rows_from(A, m0), B, beta,
+                      rows_from(C, m0), c->s_tc.p, need, c->s_kpart.c(),
+                      c->s_kpart.bytes / sizeof(cplx), c->err.as<int>(), nullptr);
+        }
+        return;
+      }
+    }
+    size_t need = ns ? slice_workspace_bytes(M, N, K, ns, bc != nullptr)
+                     : tc_workspace_bytes(M, N, K, 3);
     c->s_tc.ensure(need);
     for (int z = 0; z < batch; ++z) {
       View a = A, b = B, cc = C;
@@ -304,7 +337,7 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
       if (ns)
         zgemm_slice(c->stream, ns, M, N, K, alpha, a, b, beta, cc, c->s_tc.p,
                     need, c->s_kpart.c(), c->s_kpart.bytes / sizeof(cplx),
-                    c->err.as<int>(), batch == 1 ? b_cache(c, ns, M, N, K, b) : nullptr);
+                    c->err.as<int>(), bc);
       else
         zgemm_tc(c->stream, 3, M, N, K, alpha, a, b, beta, cc, c->s_tc.p, need,
                  c->s_kpart.c(), c->s_kpart.bytes / sizeof(cplx),
@@ -593,21 +626,23 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
   c->s_Y.ensure((size_t)g * N1L * sizeof(cplx));
   cplx* Yt = c->s_big1.c();  // [q][I][a][j][b]
   cplx* G = c->s_big2.c();   // [q][(I,a)][(j,b)]
-  cplx* S = c->s_S.c();      // [(q,I,a)][P]
+  cplx* S = c->s_S.c();      // [(q,I)][P][a]
   cplx* Y = c->s_Y.c();      // [(q,I,a)][P]
   if (mode != SIG_FWD) {
     for (int q = 0; q < g; ++q)
       unpack_doubles(c->stream, x + q * N + N1, nc, nw, v, Yt + q * N1wv);
-    // S[(q,I,a)][P] = sum_{jb} y_{Ijab} B^P_{jb}
+    // S[(q,I,a)][P] = sum_{jb} y_{Ijab} B^P_{jb}, stored as [(q,I)][P][a]
+    // (the tile epilogue's lanes, consecutive a, write consecutive elements)
     gemm(c, prec, (int)(g * N1), L, (int)wv, 1.0, view(Yt, wv, 1),
          rows2(view(B + (int64_t)nc * n + o, 0, nn), n, 1, v), 0.0,
-         view(S, L, 1));
+         rows2(view(S, 0, v), vL, 1, v), 1, true);
     // sigma1 (M12 x2), the <ab||cj> part, transposed so that the long side
-    // (c) is the row dimension: sigma1^T[c][(q, K)] = -sum_{(a,P)} B^P_ca
-    // S[(q,K,a)][P]
+    // (c) is the row dimension: sigma1^T[c][(q, K)] = -sum_{(P,a)} B^P_ca
+    // S[(q,K)][P][a]; the contraction index (P, a) runs contiguously through
+    // both B^P_c. and S
     const View s1rows = rows2(view(sig, 0, 1), N, v, nc);
     gemm(c, prec, v, g * nc, (int)vL, -1.0,
-         cols2(view(B + (int64_t)o * n + o, n, 0), 1, nn, L), trans(view(S, vL, 1)),
+         cols2(view(B + (int64_t)o * n + o, n, 0), nn, 1, v), view(S, 1, vL),
          0.0, trans(s1rows));
     // the <Kb||Ij> part: sigma1[K][c] += sum_{Ijb} y_{Ijcb} conj(h[K][b][I][j]),
     // rows (q, c), columns K
@@ -626,11 +661,12 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
   // <Kb||Ij> part is added while packing)
   gemm(c, prec, (int)(g * N1), (int)wv, L, 1.0, view(Y, L, 1),
        cols2(view(B + (int64_t)o * n + nc, nn, 0), 1, n, v), 0.0,
-       view(G, wv, 1));
+       view(G, wv, 1), 1, true);
   for (int q = 0; q < g; ++q)
     sigma2_finish(c->stream, G + q * N1wv,
                   mode == SIG_FWD ? nullptr : x + q * N + N1, x + q * N,
-                  c->h1.c(), c->eps.d(), nc, nw, v, sig + q * N + N1);
+                  c->h1.c(), c->eps.d(), nc, nw, v, sig + q * N + N1,
+                  prec == CVSADC_FP64);
   if (mode == SIG_FWD) return;
   // sigma1 += M11 x1 (dense product, FP64 for the small block)
   gemm64(c, (int)N1, g, (int)N1, 1.0, view(c->M11.c(), N1, 1), view(x, 1, N),

@@ -68,6 +68,17 @@ def test_zgemm_slices_against_numpy(ctx, shape, prec, tol):
     assert err.max() < tol, err.max()
 
 
+@pytest.mark.parametrize("shape", [(1300, 1, 2000), (2000, 3, 5000), (5000, 8, 700)])
+def test_fp64_few_columns_against_numpy(ctx, shape):
+    # N <= 8 with A's rows contiguous: the FP64 engine's warp-per-row path
+    M, N, K = shape
+    rng = np.random.default_rng(M + N + K)
+    A, B = _rand(rng, M, K), _rand(rng, K, N)
+    ref = A @ B
+    bound = np.abs(A) @ np.abs(B)
+    assert (np.abs(ctx.zgemm(A, B, "fp64") - ref) / bound).max() < 1e-13
+
+
 def test_slice_accumulation_does_not_grow_with_k(ctx):
     # positive data: every partial sum has the sign of the total, so any
     # rounding in the accumulation shows up in full
