@@ -320,6 +320,18 @@ int cvsadc_kernel_stats(int32_t kernel, int64_t* launches, double* ms,
                         double* flops);
 void cvsadc_kernel_stats_reset(void);
 
+/* The error path of the bounded device waits, on demand (the paper has no
+ * counterpart: a service for failure handling).  Every wait inside the
+ * library's kernels (mbarrier phases of the tensor-core pipelines) gives up
+ * after 4 s of the GPU's global timer, records a code and lets its kernel
+ * return, so that a stuck pipeline surfaces as CVSADC_ETIMEOUT instead of a
+ * hang.  This call runs one such wait on an mbarrier that nothing arrives
+ * on, with limit_ns (clamped to [1 ms, 4 s]), on the context's stream.
+ * Returns CVSADC_ETIMEOUT (the wait expired, the context stays usable and
+ * its error flag is cleared), CVSADC_EINVAL for a NULL context, or
+ * CVSADC_ECUDA. */
+int cvsadc_wait_probe(cvsadc_ctx* ctx, int64_t limit_ns);
+
 /* --------------------------------------------------------------------
  * Allocation-free small-output GEMM.  The paper has no counterpart: this
  * is a service for callers that must not let a library allocate device

@@ -185,6 +185,12 @@ class Context:
         self._check(self.lib.cvsadc_sigma(self.h, prec, flags, px, po, nvec))
         return out
 
+    def wait_probe(self, limit_ns):
+        """Run one bounded device wait that nothing satisfies (limit clamped
+        to [1 ms, 4 s]); raises CvsadcError(CVSADC_ETIMEOUT) when it expires
+        as designed.  The context stays usable."""
+        self._check(self.lib.cvsadc_wait_probe(self.h, int(limit_ns)))
+
     def zgemm(self, A, B, precision="fp64"):
         """C = A B (complex) with the library's GEMM engines."""
         prec = PRECISIONS[precision] if isinstance(precision, str) else precision
@@ -415,10 +421,15 @@ def energy_function(ctx, ncore, nval, nvirt, nroots, precision="fp64", conv=1e-8
     class CVSADCEnergy(torch.autograd.Function):
         @staticmethod
         def forward(fctx, eps, B):
-            omega, ge, gB = ctx.grad(eps.contiguous(), B.contiguous(), ncore, nval,
-                                     nvirt, nroots, conv=conv, precision=precision)
-            fctx.save_for_backward(ge, gB)
-            return omega.sum()
+            # the adjoint pass runs only when a gradient can be asked for
+            if fctx.needs_input_grad[0] or fctx.needs_input_grad[1]:
+                omega, ge, gB = ctx.grad(eps.contiguous(), B.contiguous(), ncore, nval,
+                                         nvirt, nroots, conv=conv, precision=precision)
+                fctx.save_for_backward(ge, gB)
+                return omega.sum()
+            out = ctx.solve(eps.contiguous(), B.contiguous(), None, ncore, nval, nvirt,
+                            nroots, precision=precision, conv=conv)
+            return torch.as_tensor(out["omega"], device=eps.device).sum()
 
         @staticmethod
         def backward(fctx, gE):

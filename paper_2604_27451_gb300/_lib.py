@@ -106,6 +106,7 @@ _SIGNATURES = {
                                            ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double)]),
     "cvsadc_kernel_stats_reset": (None, []),
+    "cvsadc_wait_probe": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "cvsadc_zgemm": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int64,
                                     _vp, ctypes.c_int64, _vp, ctypes.c_int64]),

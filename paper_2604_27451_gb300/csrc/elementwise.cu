@@ -1167,6 +1167,25 @@ void scale_vectors(cudaStream_t s, cplx* x, const double* scale, int k,
 }
 
 
+__global__ void gather_columns_kernel(const cplx* __restrict__ src, int rows, int64_t lds,
+                                      const int* __restrict__ idx, int ncols,
+                                      cplx* __restrict__ dst, int64_t ldd) {
+  const int64_t total = (int64_t)rows * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ncols), q = (int)(e % ncols);
+    dst[(int64_t)r * ldd + q] = src[(int64_t)r * lds + idx[q]];
+  }
+}
+
+void gather_columns(cudaStream_t s, const cplx* src, int rows, int64_t lds, const int* idx,
+                    int ncols, cplx* dst, int64_t ldd) {
+  if (rows <= 0 || ncols <= 0) return;
+  gather_columns_kernel<<<grid1d((int64_t)rows * ncols, 256), 256, 0, s>>>(
+      src, rows, lds, idx, ncols, dst, ldd);
+  CVS_CHECK_LAUNCH();
+}
+
 void copy_view(cudaStream_t s, int M, int N, double alpha, View src,
                View dst) {
   copy_view_kernel<<<grid1d((int64_t)M * N, 256), 256, 0, s>>>(M, N, alpha,

@@ -116,12 +116,29 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 // bounded wait on the phase with the given parity: try_wait suspends the
 // thread in hardware for a while before it reports "not yet", so the loop
 // polls without sleeping and reads the clock only every 64 tries
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// true once the phase completes; false after limit_ns of the global timer
+__device__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtime();
   for (uint32_t n = 1;; ++n) {
     if (mbar_try(bar, parity)) return true;
-    if ((n & 63) == 0 && gtime() - t0 > WAIT_NS) return false;
+    if ((n & 63) == 0 && gtime() - t0 > limit_ns) return false;
+  }
+}
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_for(bar, parity, WAIT_NS);
+}
+
+// The error path of the bounded waits, on demand: one thread waits, with
+// limit_ns, on an mbarrier that nothing arrives on.  The wait gives up, the
+// kernel records code 5 in *err (as a GEMM's expired wait records its
+// code) and returns.
+__global__ void wait_probe_kernel(uint64_t limit_ns, int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait_for(&bar, 0, limit_ns)) atomicExch(err, 5);
   }
 }
 __device__ __forceinline__ void tma_load(const CUtensorMap* map, uint64_t* bar,
@@ -1237,6 +1254,13 @@ SDims sdims_of(int M, int N, int K, int nslices, bool b_cached) {
 }
 
 }  // namespace
+
+void wait_probe(cudaStream_t s, int64_t limit_ns, int* err) {
+  const uint64_t lim = (uint64_t)std::min<int64_t>(std::max<int64_t>(limit_ns, 1000000),
+                                                   (int64_t)WAIT_NS);
+  wait_probe_kernel<<<1, 32, 0, s>>>(lim, err);
+  CVS_CHECK_LAUNCH();
+}
 
 size_t slice_workspace_bytes(int M, int N, int K, int nslices, bool b_cached) {
   SDims d = sdims_of(M, N, K, nslices, b_cached);

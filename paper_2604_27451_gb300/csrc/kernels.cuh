@@ -30,6 +30,9 @@ bool tc_available();
 // Exact-accumulation slice GEMM on the tensor cores (see gemm_tc.cu):
 // nslices = 4 (10 slice products, ~2^-28 of row max x column max) or 7
 // (28 products, FP64 class).
+// one bounded wait that expires after limit_ns (clamped to [1 ms, 4 s]) and
+// records its code in *err
+void wait_probe(cudaStream_t s, int64_t limit_ns, int* err);
 // workspace of one call (b_cached: B comes from a SliceBCache)
 size_t slice_workspace_bytes(int M, int N, int K, int nslices, bool b_cached = false);
 // Packed slices (and column exponents) of a B operand that does not change
@@ -133,6 +136,10 @@ void ts_subtract(cudaStream_t s, const cplx* V, int m, const cplx* c,
 void scale_vectors(cudaStream_t s, cplx* x, const double* scale, int k,
                    int64_t N);
 // generic strided copy dst(r, c) = alpha * src(r, c)
+// dst[r][q] = src[r][idx[q]] (row-major, leading dimensions lds / ldd;
+// idx a device array of ncols column indices)
+void gather_columns(cudaStream_t s, const cplx* src, int rows, int64_t lds, const int* idx,
+                    int ncols, cplx* dst, int64_t ldd);
 void copy_view(cudaStream_t s, int M, int N, double alpha, View src, View dst);
 // indices of the k smallest entries of d[N] (ascending), k <= 64
 void k_smallest(cudaStream_t s, const double* d, int64_t N, int k,

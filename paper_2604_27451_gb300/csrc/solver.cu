@@ -727,11 +727,12 @@ void build_fns(cvsadc_ctx* c, int prec, double tau) {
   CVS_CUDA(cudaMemcpyAsync(c->fns_occ.p, occ_desc.data(), v * sizeof(double),
                            cudaMemcpyHostToDevice, c->stream));
   // V~ columns (descending occupation order) gathered into Vt [v][vk]
-  DBuf Vt;
+  DBuf Vt, kidx;
   Vt.ensure((size_t)v * vk * sizeof(cplx));
-  for (int q = 0; q < vk; ++q)
-    copyv(c, v, 1, 1.0, view(Vec.c() + keep[q], v, 1),
-              view(Vt.c() + q, vk, 1));
+  kidx.ensure((size_t)vk * sizeof(int));
+  CVS_CUDA(cudaMemcpyAsync(kidx.p, keep.data(), (size_t)vk * sizeof(int),
+                           cudaMemcpyHostToDevice, c->stream));
+  gather_columns(c->stream, Vec.c(), v, v, (const int*)kidx.p, vk, Vt.c(), vk);
   // F^NS = V~^H diag(eps_v) V~ (Eq. 18): scale rows of V~ by eps_v, GEMM
   DBuf EV, Fns, Fh, Z, et;
   EV.ensure((size_t)v * vk * sizeof(cplx));
@@ -759,18 +760,16 @@ void build_fns(cvsadc_ctx* c, int prec, double tau) {
     DBuf tmp;
     tmp.ensure((size_t)nmat * n * vk * sizeof(cplx));
     const cplx* U = c->fns_U.c();
-    // oo block copy
-    for (int64_t P = 0; P < nmat; ++P)
-      copyv(c, o, o, 1.0, view(src + P * nn, n, 1),
-                view(dst.c() + P * nn2, n2, 1));
+    // oo block copy, rows (P, i) of all matrices at once
+    copyv(c, (int)(nmat * o), o, 1.0, rows2(view(src, 0, 1), nn, n, o),
+          rows2(view(dst.c(), 0, 1), nn2, n2, o));
     // tmp[P][p][b'] = sum_b src[P][p][o+b] U[b][b']   (all rows p)
     gemm(c, CVSADC_FP64, n, vk, v, 1.0,
          batched(view(src + o, n, 1), nn), view(U, vk, 1), 0.0,
          batched(view(tmp.p, vk, 1), (int64_t)n * vk), (int)nmat);
-    // ov block: rows i < o
-    for (int64_t P = 0; P < nmat; ++P)
-      copyv(c, o, vk, 1.0, view(tmp.c() + P * n * vk, vk, 1),
-                view(dst.c() + P * nn2 + o, n2, 1));
+    // ov block: rows i < o of every matrix
+    copyv(c, (int)(nmat * o), vk, 1.0, rows2(view(tmp.c(), 0, 1), (int64_t)n * vk, vk, o),
+          rows2(view(dst.c() + o, 0, 1), nn2, n2, o));
     // vv block: U^H tmp[P][o:][:]
     gemm(c, CVSADC_FP64, vk, vk, v, 1.0,
          conj_of(trans(view(U, vk, 1))),
@@ -3092,6 +3091,11 @@ void cvsadc_kernel_stats_reset(void) {
 
 int64_t cvsadc_launch_count(void) {
   return (int64_t)__atomic_load_n(&g_launch_count, __ATOMIC_RELAXED);
+}
+
+int cvsadc_wait_probe(cvsadc_ctx* c, int64_t limit_ns) {
+  if (!c) return CVSADC_EINVAL;
+  return guarded(c, [&] { wait_probe(c->stream, limit_ns, c->err.as<int>()); });
 }
 
 int cvsadc_zgemm(cvsadc_ctx* c, int32_t precision, int32_t flags, int32_t M,

@@ -1,6 +1,7 @@
 """GPU edge cases: the smallest partitions the method allows, every root
 of a problem, an empty batch and a root count beyond the space — each
-against the oracle's exact answer or the documented error."""
+against the oracle's exact answer or the documented error — and the error
+path of the bounded device waits."""
 
 import numpy as np
 import pytest
@@ -63,4 +64,27 @@ def test_more_roots_than_singles_with_the_preconditioner():
     ref = osolve.solve(inst.eps, inst.B, inst.dip, nc, nw, nv, 5, method="dense",
                        want_vectors=False)
     assert np.abs(out["omega"] - ref["omega"]).max() < 1e-9
+    ctx.close()
+
+
+def test_bounded_wait_expires_with_etimeout():
+    """A bounded device wait that nothing satisfies gives up after its limit
+    and surfaces as CVSADC_ETIMEOUT; the kernel returns, so the context
+    (and its error flag) is usable for the next call."""
+    import time
+
+    import paper_2604_27451_gb300 as pkg
+    from paper_2604_27451_gb300._lib import CVSADC_ETIMEOUT
+
+    ctx = pkg.Context(0)
+    t0 = time.perf_counter()
+    with pytest.raises(pkg.CvsadcError) as ei:
+        ctx.wait_probe(200_000_000)
+    assert ei.value.code == CVSADC_ETIMEOUT
+    assert time.perf_counter() - t0 >= 0.2
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((300, 400)) + 1j * rng.standard_normal((300, 400))
+    B = rng.standard_normal((400, 200)) + 1j * rng.standard_normal((400, 200))
+    C = ctx.zgemm(A, B, "slice4")
+    assert (np.abs(C - A @ B) / (np.abs(A) @ np.abs(B))).max() < 1e-6
     ctx.close()

@@ -52,6 +52,9 @@ def test_gradient_finite_differences_and_autograd_function():
     Fn = pkg.energy_function(ctx, nc, nw, nv, k, precision="slice4", conv=1e-10)
     E = Fn.apply(eps, B)
     E.backward()
+    with torch.no_grad():  # inputs without gradients: the solve alone, same energy
+        E0 = Fn.apply(eps.detach(), B.detach())
+    assert abs(E0.item() - E.item()) < 1e-9
     rng = np.random.default_rng(4)
     d = rng.standard_normal(inst.B.shape) + 1j * rng.standard_normal(inst.B.shape)
     d = 0.5 * (d + np.conj(d.transpose(0, 2, 1)))
