@@ -968,7 +968,12 @@ __global__ void slice_pack_b(View B, int K, int k0, int N, int Np2, int Kp,
 // a run is 2 K blocks x 2 parts: at most 4 pairs x 256 products of
 // |q q'| <= 2^13 (2^14 for order 0, one pair) per element, so every run
 // sums exactly in FP32.  TMEM: 2 buffers x 4 orders x 64 columns = 512.
-// The drain adds each order, times its scale, to float-float accumulators.
+// The B tiles of a stage lie back to back (one 256-row K-major operand) and
+// the orders of a buffer side by side, so the pairs (i, 0..3-i) are one MMA
+// of A_i with B_0..B_{3-i} (N = 64 (4 - i)) into orders i..3: four MMAs
+// per K step instead of ten, and each A tile is read from shared memory
+// once.  The drain adds each order, times its scale, to float-float
+// accumulators.
 //
 // CTA: 576 threads, tile 128 x 64 (N' = 64: 32 complex columns).  Warp 0
 // lane 0: TMA producer; warp 1 lane 0: MMA issuer; warps 2..17: drain (warp
@@ -1058,7 +1063,10 @@ __global__ void __launch_bounds__(576, 1)
   } else if (threadIdx.x == 32) {
     // MMA issuer: for each unit, the ten pairs into their order's
     // accumulator of the run's buffer
-    const uint32_t id = idesc_bf16(BM, RBN);
+    // N = 64 (4 - i) for the MMA of A_i
+    uint32_t idn[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) idn[i] = idesc_bf16(BM, RBN * (4 - i));
     for (int r = 0; r < nruns && !fail; ++r) {
       const int b = r & 1;
       if (r >= 2 && !mbar_wait(&aempty[b], ((r >> 1) + 1) & 1)) {
@@ -1076,19 +1084,17 @@ __global__ void __launch_bounds__(576, 1)
         }
         fence_after();
         const uint32_t st = smem_u32(smem + s * R_STAGE);
+        const uint64_t bd = sdesc(st + 4 * R_A_TILE);  // B_0 .. B_3
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const uint32_t dt = tmem + (uint32_t)((b * 4 + o) * RBN);
+        for (int i = 0; i < 4; ++i) {
+          // pairs (i, 0 .. 3 - i) into orders i .. 3; the first MMA of a
+          // run (i = 0 covers every order) starts the accumulators
+          const uint32_t dt = tmem + (uint32_t)((b * 4 + i) * RBN);
+          const uint64_t ad = sdesc(st + i * R_A_TILE);
 #pragma unroll
-          for (int i = 0; i <= o; ++i) {
-            const int j = o - i;
-            const uint64_t ad = sdesc(st + i * R_A_TILE);
-            const uint64_t bd = sdesc(st + 4 * R_A_TILE + j * R_B_TILE);
-#pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-              umma(dt, ad + 2 * kk, bd + 2 * kk, id,
-                   (u != u0 || i != 0 || kk != 0) ? 1u : 0u);
-          }
+          for (int kk = 0; kk < BK / 16; ++kk)
+            umma(dt, ad + 2 * kk, bd + 2 * kk, idn[i],
+                 (u != u0 || i != 0 || kk != 0) ? 1u : 0u);
         }
         umma_commit(&empty[s]);
       }
