@@ -378,11 +378,18 @@ def extras(args, state, inst, stream, torch, pkg):
     res = {}
     ctx, X = state["ctx"], state["X"]
     dev = X.device
+    only_large = args.ttr_large_only
+    if only_large:
+        state.clear()
+        del X
+        ctx.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
     # sigma builds/s of the other precisions on (part of) the same block;
     # FP64 FMA runs at ~1.1 TFLOP/s on this GPU: one vector is minutes at the
     # large workload, so it is timed on the medium solve below instead
     rates = {}
-    for p, nvec in (("bf16x3", NVEC), ("slice4", NVEC), ("fp64_slice7", 2)):
+    for p, nvec in () if only_large else (("bf16x3", NVEC), ("slice4", NVEC), ("fp64_slice7", 2)):
         xs = X[:nvec].contiguous()
         ss = torch.empty_like(xs)
         ctx.sigma(xs, p, out=ss)
@@ -395,8 +402,43 @@ def extras(args, state, inst, stream, torch, pkg):
         torch.cuda.synchronize()
         rates[p] = round(nvec / (e0.elapsed_time(e1) / 1e3), 3)
         del xs, ss
-    res["sigma_builds_per_s"] = rates
-    # e2e: the public API with host buffers (pinned), copies inside
+    if not only_large:
+        res["sigma_builds_per_s"] = rates
+        res.update(_e2e_and_release(args, state, X, ctx, torch))
+        del X
+
+    # time-to-roots: full solves (prepare + Davidson + refinement) with
+    # inputs resident, mixed vs FP64; the Schur-complement preconditioner
+    # is on unless the entry says "diag"
+    def solve_entry(e_, B_, d_, w, p, precond="schur", conv=1e-7, refine=True):
+        c2 = pkg.Context(dev.index, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = c2.solve(e_, B_, d_, w["ncore"], w["nval"], w["nvirt"], w["nroots"],
+                     precision=p, conv=conv, precond=precond, refine=refine)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        c2.close()
+        i = o["info"]
+        return o["omega"].cpu().numpy(), {
+            "s": round(dt, 3), "status": int(o["status"]), "iterations": i["iterations"],
+            "sigma_vectors": i["sigma_vectors"], "coupling_vectors": i["coupling_vectors"],
+            "schur_builds": i["schur_builds"], "t_schur_s": round(i["t_schur_ms"] / 1e3, 3),
+            "t_prepare_s": round(i["t_prepare_ms"] / 1e3, 3)}
+
+    if not only_large:
+        res.update(_small_medium_ttr(args, dev, torch, solve_entry))
+    if args.ttr_large:
+        res.update(_large_ttr(args, inst, dev, torch, solve_entry))
+    if not args.no_cpu_baseline and not only_large:
+        res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds, rows=max(1, inst.nvirt // 8))
+    return res
+
+
+def _e2e_and_release(args, state, X, ctx, torch):
+    """e2e: the public API with host buffers (pinned), copies inside; then
+    the prepared context and the trial block are released."""
+    res = {}
     N = X.shape[1]
     xh = torch.empty((NVEC, N), dtype=torch.complex128, pin_memory=True)
     xh.copy_(X)
@@ -414,30 +456,15 @@ def extras(args, state, inst, stream, torch, pkg):
                   "path": "cvsadc_sigma through the C ABI with pinned host buffers"}
     del xh, sh, xn, sn
     state.clear()
-    del X
     ctx.close()
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
+    return res
 
-    # time-to-roots: full solves (prepare + Davidson + refinement) with
-    # inputs resident, mixed vs FP64; the Schur-complement preconditioner
-    # is on unless the entry says "diag"
-    def solve_entry(e_, B_, d_, w, p, precond="schur", conv=1e-7):
-        c2 = pkg.Context(dev.index, stream=stream.cuda_stream)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        o = c2.solve(e_, B_, d_, w["ncore"], w["nval"], w["nvirt"], w["nroots"],
-                     precision=p, conv=conv, precond=precond)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        c2.close()
-        i = o["info"]
-        return o["omega"].cpu().numpy(), {
-            "s": round(dt, 3), "status": int(o["status"]), "iterations": i["iterations"],
-            "sigma_vectors": i["sigma_vectors"], "coupling_vectors": i["coupling_vectors"],
-            "schur_builds": i["schur_builds"], "t_schur_s": round(i["t_schur_ms"] / 1e3, 3),
-            "t_prepare_s": round(i["t_prepare_ms"] / 1e3, 3)}
 
+def _small_medium_ttr(args, dev, torch, solve_entry):
+    """Time-to-roots on the small and medium workloads, mixed vs FP64."""
+    res = {}
     w = WORKLOADS["small"]
     sm = make_instance(w["ncore"], w["nval"], w["nvirt"], w["naux"], seed=0)
     e_, B_, d_ = (torch.from_numpy(a).to(dev) for a in (sm.eps, sm.B, sm.dip))
@@ -471,6 +498,12 @@ def extras(args, state, inst, stream, torch, pkg):
     res["time_to_roots_medium"] = ttm
     del e_, B_, d_, me
     torch.cuda.empty_cache()
+    return res
+
+
+def _large_ttr(args, inst, dev, torch, solve_entry):
+    """Time-to-roots on the large workload (the doubles-folded solver)."""
+    res = {}
     if args.ttr_large:
         # the large workload itself: the full-space subspace does not fit, so
         # the doubles-folded solver runs (singles-space vectors only)
@@ -482,17 +515,19 @@ def extras(args, state, inst, stream, torch, pkg):
                                wl["ncore"], wl["nval"], wl["nvirt"], wl["naux"], wl["nroots"])}
         rl = {}
         for p in args.ttr_large.split(","):
-            rl[p], ttl[p] = solve_entry(e_, B_, None, wl, p, conv=1e-6)
+            rl[p], ttl[p] = solve_entry(e_, B_, None, wl, p.replace("_norefine", ""), conv=1e-6,
+                                        refine=not p.endswith("_norefine"))
+        # every entry against the FP64-class (7-slice) solve
+        ref_key = "fp64_slice7"
         for p in rl:
-            if p != "slice4" and "slice4" in rl:
-                ttl["max_abs_root_diff_slice4_vs_%s_Eh" % p] = float(np.abs(rl["slice4"] - rl[p]).max())
-                ttl["speedup_slice4_vs_%s" % p] = round(ttl[p]["s"] / ttl["slice4"]["s"], 2)
+            if p != ref_key and ref_key in rl:
+                ttl["max_abs_root_diff_%s_vs_%s_Eh" % (p, ref_key)] = float(
+                    np.abs(rl[p] - rl[ref_key]).max())
+                ttl["speedup_%s_vs_%s" % (p, ref_key)] = round(ttl[ref_key]["s"] / ttl[p]["s"], 2)
         ttl["roots_Eh"] = {p: [round(float(x), 9) for x in r] for p, r in rl.items()}
         res["time_to_roots_large"] = ttl
         del e_, B_
         torch.cuda.empty_cache()
-    if not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(inst, args.cpu_seconds, rows=max(1, inst.nvirt // 8))
     return res
 
 
@@ -615,7 +650,10 @@ def main():
                     help="also time the FP64 solve of the medium workload (minutes)")
     ap.add_argument("--ttr-large", default="",
                     help="comma-separated precisions whose full solve of the large "
-                         "workload is timed (e.g. slice4,fp64_slice7)")
+                         "workload is timed (e.g. slice4,fp64_slice7; a _norefine "
+                         "suffix skips the FP64-class continuation)")
+    ap.add_argument("--ttr-large-only", action="store_true",
+                    help="after the timed steps, only the --ttr-large solves")
     ap.add_argument("--profile-gemm", action="store_true",
                     help="run one 4096^3 complex GEMM three times (ncu case)")
     args = ap.parse_args()

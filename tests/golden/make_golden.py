@@ -26,13 +26,16 @@ def small():
     M11 = adc2.m11(inst.eps, inst.B, nc, nw, nv, t2=t2)
     M21 = adc2.m21(inst.eps, inst.B, nc, nw, nv)
     d22 = adc2.m22(inst.eps, nc, nw, nv)
-    w_, X = adc2.eig_partitioned(M11, M21, d22, w["nroots"])
+    w_, X = adc2.eig_partitioned(M11, M21, d22, w["nroots"] + 1)
+    omega_next = float(w_[-1])  # root k + 1: the gap of root k (eigenvector bounds)
+    w_, X = w_[:-1], X[:-1]
     F = adc2.transition_moments(inst.eps, inst.B, inst.dip, nc, nw, nv, t2=t2)
     f = adc2.oscillator_strengths(w_, X, F)
     out = dict(
         source="oracle: exact Lowdin-partitioned eigenvalues of the explicit "
                "CVS-ADC(2) matrix (oracle/adc2.py), seeded synthetic inputs",
         shape=w, seed=0, emp2=float(e2), omega=[float(x) for x in w_],
+        omega_next=omega_next,
         osc=[float(x) for x in f],
         singles_weight=[float(np.sum(np.abs(X[k, :M11.shape[0]]) ** 2)) for k in range(len(w_))],
     )
