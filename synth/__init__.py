@@ -14,4 +14,5 @@ from .generate import (  # noqa: F401
     make_kramers_instance,
     make_spinfree_instance,
     batched_shapes,
+    physical_scale,
 )

@@ -16,15 +16,18 @@ same structure stand in for them:
 * virtual energies are U(0.05, 2.5);
 * every Cholesky vector B^P is Hermitian, B^P_pq = conj(B^P_qp), with
   N(0,1) + i N(0,1) off-diagonal entries and N(0,1) real diagonal entries,
-  scaled by ``scale * exp(-P / decay)``.  By default ``scale`` is
-  0.34 (max(nval, 1) nvirt^2)^(-1/4): dense random couplings sum over all
-  nval nvirt^2 doubles a singles state talks to, so a fixed scale would let
-  the second-order terms grow with the size until they dwarf the excitation
-  energies.  With this scale the coupling a singles state feels stays
-  bounded, E_MP2 grows with the number of occupied spinors (extensive), and
-  the core excitations look like the paper's: on the small workload the
-  lowest roots lie 0.2 Eh below the bare core -> virtual gaps and 0.7 Eh
-  below the lowest doubles, with singles weights of about 0.87;
+  scaled by ``scale * exp(-P / decay)``, scale 0.3 as the named workloads
+  state it.  That scale is far from perturbative (small workload: E_MP2 =
+  -2e4 Eh, roots near 15 Eh with 1.7 % singles weight, far below the lowest
+  M22 entry), and it gets worse with the size, because dense random
+  couplings sum over all nval nvirt^2 doubles a singles state talks to.
+  ``physical_scale(nval, nvirt)`` = 0.34 (max(nval, 1) nvirt^2)^(-1/4) keeps
+  the coupling a singles state feels bounded, so that E_MP2 grows with the
+  number of occupied spinors (extensive) and the core excitations look like
+  the paper's: on the small workload the lowest roots lie 0.2 Eh below the
+  bare core -> virtual gaps and 0.7 Eh below the lowest doubles, with
+  singles weights of about 0.87 (a companion instance, not a named
+  workload);
 * the three dipole matrices use the same Hermitian construction with scale
   0.1.
 
@@ -103,19 +106,17 @@ def _hermitian(rng: np.random.Generator, n: int, scale: float) -> np.ndarray:
     return out
 
 
-def default_scale(nval: int, nvirt: int) -> float:
+def physical_scale(nval: int, nvirt: int) -> float:
     """The size-aware Cholesky-vector scale described above."""
     return 0.34 * (max(nval, 1) * nvirt * nvirt) ** -0.25
 
 
 def make_instance(ncore: int, nval: int, nvirt: int, naux: int, seed: int = 0,
-                  scale: float | None = None, decay: float = 60.0,
+                  scale: float = 0.3, decay: float = 60.0,
                   dip_scale: float = 0.1) -> Instance:
     """Seeded synthetic instance with the structure described above."""
     if ncore < 1 or nval < 0 or nvirt < 2 or naux < 1:
         raise ValueError("bad partition sizes")
-    if scale is None:
-        scale = default_scale(nval, nvirt)
     rng = np.random.default_rng(seed)
     e_core = core_energies(ncore, rng)
     npair = (nval + 1) // 2
