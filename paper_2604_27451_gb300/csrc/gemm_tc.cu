@@ -990,8 +990,8 @@ constexpr int R_RUN = 4;                 // units (K block, part) per exact run
 
 __global__ void __launch_bounds__(576, 1)
     tc_slice4r_kernel(const __grid_constant__ CUtensorMap tmA,
-                      const __grid_constant__ CUtensorMap tmB, int Kp, int kpb,
-                      int kb_off, int nkb, int zl, int M, int N,
+                      const __grid_constant__ CUtensorMap tmB, int kpa, int ka_off,
+                      int kpb, int kb_off, int nkb, int zl, int M, int N,
                       const int* __restrict__ eA,
                       const int* __restrict__ eB, double alpha, double beta,
                       View C, cplx* part, int* err) {
@@ -1054,7 +1054,8 @@ __global__ void __launch_bounds__(576, 1)
       mbar_expect_tx(&full[s], R_STAGE);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        tma_load(&tmA, &full[s], st + i * R_A_TILE, (2 * i + c) * Kp + kb * BK, m0);
+        tma_load(&tmA, &full[s], st + i * R_A_TILE, (2 * i + c) * kpa + (ka_off + kb) * BK,
+                 m0);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         tma_load(&tmB, &full[s], st + 4 * R_A_TILE + j * R_B_TILE,
@@ -1241,7 +1242,7 @@ struct SDims {
   int Mp, Np2, npairs, nseg, kc, KpF;
   size_t a_bytes, b_bytes, e_bytes;
 };
-SDims sdims_of(int M, int N, int K, int nslices, bool b_cached) {
+SDims sdims_of(int M, int N, int K, int nslices, bool b_cached, bool a_cached = false) {
   SDims d;
   const int tn = nslices == 4 ? RBN : SBN;
   d.Mp = (M + BM - 1) / BM * BM;
@@ -1249,11 +1250,11 @@ SDims sdims_of(int M, int N, int K, int nslices, bool b_cached) {
   d.npairs = nslices * (nslices + 1) / 2;
   d.nseg = nslices == 4 ? 8 : 2 * d.npairs;
   d.KpF = (int)(((int64_t)K + BK - 1) / BK * BK);
-  const size_t per_k = (size_t)(d.Mp + (b_cached ? 0 : d.Np2)) * d.nseg * 2;
-  int64_t kc = (int64_t)(PACK_BUDGET / per_k) / BK * BK;
+  const size_t per_k = (size_t)((a_cached ? 0 : d.Mp) + (b_cached ? 0 : d.Np2)) * d.nseg * 2;
+  int64_t kc = per_k ? (int64_t)(PACK_BUDGET / per_k) / BK * BK : (int64_t)d.KpF;
   kc = std::max<int64_t>(kc, BK);
   d.kc = (int)std::min<int64_t>(kc, d.KpF);
-  d.a_bytes = (size_t)d.Mp * d.nseg * d.kc * 2;
+  d.a_bytes = a_cached ? 0 : (size_t)d.Mp * d.nseg * d.kc * 2;
   d.b_bytes = b_cached ? 0 : (size_t)d.Np2 * d.nseg * d.kc * 2;
   d.e_bytes = ((size_t)d.Mp + d.Np2 / 2 + 64) * sizeof(int);
   return d;
@@ -1268,9 +1269,14 @@ void wait_probe(cudaStream_t s, int64_t limit_ns, int* err) {
   CVS_CHECK_LAUNCH();
 }
 
-size_t slice_workspace_bytes(int M, int N, int K, int nslices, bool b_cached) {
-  SDims d = sdims_of(M, N, K, nslices, b_cached);
+size_t slice_workspace_bytes(int M, int N, int K, int nslices, bool b_cached, bool a_cached) {
+  SDims d = sdims_of(M, N, K, nslices, b_cached, a_cached);
   return d.a_bytes + d.b_bytes + d.e_bytes + 256;
+}
+
+size_t slice_acache_bytes(int M, int K, int nslices) {
+  SDims d = sdims_of(M, 1, K, nslices, true, true);
+  return (size_t)d.Mp * d.nseg * d.KpF * 2 + (size_t)d.Mp * sizeof(int) + 256;
 }
 
 size_t slice_bcache_bytes(int N, int K, int nslices) {
@@ -1291,10 +1297,11 @@ int64_t slice_row_slab(int M, int N, int K, int nslices) {
 void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
                  double alpha, View A, View B, double beta, View C, void* work,
                  size_t work_bytes, cplx* part, size_t part_elems, int* err,
-                 SliceBCache* bc) {
+                 SliceBCache* bc, SliceBCache* ac) {
   if (M <= 0 || N <= 0) return;
   CVS_REQUIRE(nslices == 4 || nslices == 7, -1, "zgemm_slice: 4 or 7 slices");
-  SDims d = sdims_of(M, N, K, nslices, bc != nullptr);
+  CVS_REQUIRE(!ac || nslices == 4, -1, "zgemm_slice: cached A needs 4 slices");
+  SDims d = sdims_of(M, N, K, nslices, bc != nullptr, ac != nullptr);
   CVS_REQUIRE(work_bytes >= d.a_bytes + d.b_bytes + d.e_bytes, -1,
               "zgemm_slice: workspace too small");
   static std::once_flag attr;
@@ -1330,6 +1337,22 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
       bc->filled = true;
     }
   }
+  // the cached A: packed once over the whole K, with whole-row exponents
+  const size_t afull = (size_t)d.Mp * d.nseg * d.KpF * 2;
+  if (ac) {
+    CVS_REQUIRE(ac->bytes >= afull + (size_t)d.Mp * sizeof(int), -1,
+                "zgemm_slice: A cache too small");
+    if (!ac->filled) {
+      int* ea = (int*)((char*)ac->base + afull);
+      CVS_CUDA(cudaMemsetAsync(ea, 0x80, (size_t)d.Mp * sizeof(int), s));
+      row_exp_kernel<<<warp_tasks_grid(M, K, EXP_SEG), 256, 0, s>>>(A, M, K, 0, ea);
+      CVS_CHECK_LAUNCH();
+      slice4r_pack_a<<<warp_tasks_grid(d.Mp, d.KpF, PACK_SEG), 256, 0, s>>>(
+          A, M, K, 0, d.Mp, d.KpF, ea, (__nv_bfloat16*)ac->base);
+      CVS_CHECK_LAUNCH();
+      ac->filled = true;
+    }
+  }
   for (int k0 = 0; k0 < K; k0 += d.kc) {
     const int Kc = std::min(d.kc, K - k0);
     const int Kp = (Kc + BK - 1) / BK * BK;
@@ -1339,9 +1362,15 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
     const __nv_bfloat16* bpc = bc ? (const __nv_bfloat16*)bc->base : bp;
     const int* eBc = bc ? (const int*)((const char*)bc->base + bfull) : eB;
     const int kpb = bc ? d.KpF : Kp, kb_off = bc ? k0 / BK : 0;
-    CVS_CUDA(cudaMemsetAsync(eA, 0x80, (size_t)d.Mp * sizeof(int), s));
-    row_exp_kernel<<<warp_tasks_grid(M, Kc, EXP_SEG), 256, 0, s>>>(A, M, Kc, k0, eA);
-    CVS_CHECK_LAUNCH();
+    // A's packed slices and exponents: the cache (whole K) or this chunk's
+    const __nv_bfloat16* apc = ac ? (const __nv_bfloat16*)ac->base : ap;
+    const int* eAc = ac ? (const int*)((const char*)ac->base + afull) : eA;
+    const int kpa = ac ? d.KpF : Kp, ka_off = ac ? k0 / BK : 0;
+    if (!ac) {
+      CVS_CUDA(cudaMemsetAsync(eA, 0x80, (size_t)d.Mp * sizeof(int), s));
+      row_exp_kernel<<<warp_tasks_grid(M, Kc, EXP_SEG), 256, 0, s>>>(A, M, Kc, k0, eA);
+      CVS_CHECK_LAUNCH();
+    }
     if (!bc) {
       CVS_CUDA(cudaMemsetAsync(eB, 0x80, eb_n * sizeof(int), s));
       col_exp_kernel<<<warp_tasks_grid(N, Kc, EXP_SEG), 256, 0, s>>>(B, Kc, k0, N, eB);
@@ -1350,8 +1379,10 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
     const unsigned ga = warp_tasks_grid(d.Mp, Kp, PACK_SEG);
     const unsigned gb = grid1d((int64_t)(d.Np2 / 2) * Kp, 256);
     if (reuse) {
-      slice4r_pack_a<<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, eA, ap);
-      CVS_CHECK_LAUNCH();
+      if (!ac) {
+        slice4r_pack_a<<<ga, 256, 0, s>>>(A, M, Kc, k0, d.Mp, Kp, eA, ap);
+        CVS_CHECK_LAUNCH();
+      }
       if (!bc) {
         slice4r_pack_b<<<gb, 256, 0, s>>>(B, Kc, k0, N, d.Np2, Kp, eB, bp);
         CVS_CHECK_LAUNCH();
@@ -1367,7 +1398,7 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
     const int64_t kcols = (int64_t)d.nseg * Kp, kcols_b = (int64_t)d.nseg * kpb;
     const double beta_c = (k0 == 0) ? beta : 1.0;
     if (reuse) {
-      CUtensorMap ma = make_map(ap, d.Mp, kcols, BM);
+      CUtensorMap ma = make_map(apc, d.Mp, (int64_t)d.nseg * kpa, BM);
       CUtensorMap mb = make_map(bpc, d.Np2, kcols_b, RBN);
       const int nkb = Kp / BK;  // K blocks; a run spans two
       int sp = tc_splits(tiles, nkb, 2 * (R_RUN / 2));
@@ -1376,8 +1407,8 @@ void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
       const int nz = (nkb + zl - 1) / zl;
       dim3 grid(d.Np2 / RBN, d.Mp / BM, nz);
       const int tok = kstats_begin(s, K_TC_SLICE, 8.0 * M * N * (double)Kc);
-      tc_slice4r_kernel<<<grid, 576, R_SMEM, s>>>(ma, mb, Kp, kpb, kb_off, nkb, zl, M, N, eA,
-                                                  eBc, alpha, beta_c, C,
+      tc_slice4r_kernel<<<grid, 576, R_SMEM, s>>>(ma, mb, kpa, ka_off, kpb, kb_off, nkb, zl,
+                                                  M, N, eAc, eBc, alpha, beta_c, C,
                                                   nz > 1 ? part : nullptr, err);
       CVS_CHECK_LAUNCH();
       kstats_end(s, tok);

@@ -33,10 +33,12 @@ bool tc_available();
 // one bounded wait that expires after limit_ns (clamped to [1 ms, 4 s]) and
 // records its code in *err
 void wait_probe(cudaStream_t s, int64_t limit_ns, int* err);
-// workspace of one call (b_cached: B comes from a SliceBCache)
-size_t slice_workspace_bytes(int M, int N, int K, int nslices, bool b_cached = false);
-// Packed slices (and column exponents) of a B operand that does not change
-// between calls, over its whole K; filled by the first call that gets it.
+// workspace of one call (b_cached / a_cached: B / A comes from a SliceBCache)
+size_t slice_workspace_bytes(int M, int N, int K, int nslices, bool b_cached = false,
+                             bool a_cached = false);
+// Packed slices (and column or row exponents) of a B (or A) operand that
+// does not change between calls, over its whole K; filled by the first call
+// that gets it.
 struct SliceBCache {
   void* base = nullptr;
   size_t bytes = 0;
@@ -44,12 +46,16 @@ struct SliceBCache {
 };
 // bytes such a cache needs for a K x N operand (independent of M)
 size_t slice_bcache_bytes(int N, int K, int nslices);
+// the same for an M x K A operand (4 slices only: packed rows and row
+// exponents over the whole K)
+size_t slice_acache_bytes(int M, int K, int nslices);
 // rows per slab when a tall product is better split over M with K whole
 // (its A packs dominate and K would otherwise run in chunks); M when not
 int64_t slice_row_slab(int M, int N, int K, int nslices);
 void zgemm_slice(cudaStream_t s, int nslices, int M, int N, int K,
                  double alpha, View A, View B, double beta, View C, void* work,
-                 size_t work_bytes, cplx* part, size_t part_elems, int* err, SliceBCache* bc = nullptr);
+                 size_t work_bytes, cplx* part, size_t part_elems, int* err, SliceBCache* bc = nullptr,
+                 SliceBCache* ac = nullptr);
 
 // C = beta * C over a view
 void scale_view(cudaStream_t s, int M, int N, double beta, View C, int batch);

@@ -191,7 +191,7 @@ struct cvsadc_ctx {
     DBuf buf;
     SliceBCache sc;
   };
-  std::map<std::array<int64_t, 11>, std::unique_ptr<BEntry>> bcache;
+  std::map<std::array<int64_t, 12>, std::unique_ptr<BEntry>> bcache;
   size_t bcache_bytes = 0;
   void clear_bcache() {
     bcache.clear();
@@ -237,19 +237,21 @@ bool needs_refine(int p) {
 }
 
 // --------------------------------------------------------------- GEMM hub
-// A cache slot for the packed slices of B (whole K) when the caller asks for
-// one (a product repeated on every sigma), B is a view of the prepared B^P
-// (it does not change between calls) and the cache stays within min(25 %
-// of free memory, 48 GB); else NULL.
-constexpr double BCACHE_MAX = 48e9;
-SliceBCache* b_cache(cvsadc_ctx* c, int ns, int N, int K, const View& B) {
+// A cache slot for the packed slices of a GEMM operand (whole K) when the
+// caller asks for one (a product repeated on every sigma), the operand is a
+// view of the prepared B^P (it does not change between calls) and the
+// caches stay within min(35 % of free memory, 64 GB); else NULL.  side 0:
+// the B operand (K x N, any slice count); side 1: the A operand (M x K, 4
+// slices).
+constexpr double BCACHE_MAX = 64e9;
+SliceBCache* op_cache(cvsadc_ctx* c, int side, int ns, int MN, int K, const View& X) {
   if (!c->B.p) return nullptr;
   const cplx* b0 = c->B.c();
   const size_t nb = c->B.bytes / sizeof(cplx);
-  if (!b0 || B.p < b0 || B.p >= b0 + nb) return nullptr;
-  const size_t bytes = slice_bcache_bytes(N, K, ns);
-  const std::array<int64_t, 11> key = {(int64_t)(B.p - b0), B.rs_hi, B.rs_lo, B.r_lo,
-                                       B.cs_hi, B.cs_lo, B.c_lo, B.conj, N, K, ns};
+  if (!b0 || X.p < b0 || X.p >= b0 + nb) return nullptr;
+  const size_t bytes = side ? slice_acache_bytes(MN, K, ns) : slice_bcache_bytes(MN, K, ns);
+  const std::array<int64_t, 12> key = {side, (int64_t)(X.p - b0), X.rs_hi, X.rs_lo, X.r_lo,
+                                       X.cs_hi, X.cs_lo, X.c_lo, X.conj, MN, K, ns};
   auto it = c->bcache.find(key);
   if (it != c->bcache.end()) return &it->second->sc;
   size_t free_b = 0, total_b = 0;
@@ -257,7 +259,7 @@ SliceBCache* b_cache(cvsadc_ctx* c, int ns, int N, int K, const View& B) {
     (void)cudaGetLastError();
     return nullptr;
   }
-  if ((double)(c->bcache_bytes + bytes) > std::min(0.25 * (double)free_b, BCACHE_MAX))
+  if ((double)(c->bcache_bytes + bytes) > std::min(0.35 * (double)free_b, BCACHE_MAX))
     return nullptr;
   auto e = std::make_unique<cvsadc_ctx::BEntry>();
   e->buf.ensure(bytes);
@@ -282,10 +284,11 @@ View rows_from(View v, int64_t m0) {
   return v;
 }
 
-// cache_b: B is the same view of B^P on every call (the sigma products), so
-// its packed slices may be kept
+// cache_b / cache_a: B / A is the same view of B^P on every call (the sigma
+// products), so its packed slices may be kept
 void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
-          View B, double beta, View C, int batch = 1, bool cache_b = false) {
+          View B, double beta, View C, int batch = 1, bool cache_b = false,
+          bool cache_a = false) {
   A = checked(A);
   B = checked(B);
   C = checked(C);
@@ -302,8 +305,10 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
     CVS_REQUIRE(tc_available(), CVSADC_EINVAL,
                 "tensor-core precisions need an sm_103 GPU with tcgen05");
     const int ns = prec == CVSADC_MIXED_SLICE4 ? 4 : prec == CVSADC_FP64_SLICE7 ? 7 : 0;
-    SliceBCache* bc = (ns && batch == 1 && cache_b) ? b_cache(c, ns, N, K, B) : nullptr;
-    if (ns && batch == 1 && !bc) {
+    SliceBCache* bc = (ns && batch == 1 && cache_b) ? op_cache(c, 0, ns, N, K, B) : nullptr;
+    SliceBCache* ac =
+        (ns == 4 && batch == 1 && cache_a) ? op_cache(c, 1, ns, M, K, A) : nullptr;
+    if (ns && batch == 1 && !bc && !ac) {
       // a tall product whose A packs dominate: slabs of rows with K whole
       // (slab boundaries on the inner row extents of A and C)
       int64_t slab = slice_row_slab(M, N, K, ns);
@@ -323,7 +328,7 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
         return;
       }
     }
-    size_t need = ns ? slice_workspace_bytes(M, N, K, ns, bc != nullptr)
+    size_t need = ns ? slice_workspace_bytes(M, N, K, ns, bc != nullptr, ac != nullptr)
                      : tc_workspace_bytes(M, N, K, 3);
     c->s_tc.ensure(need);
     for (int z = 0; z < batch; ++z) {
@@ -337,7 +342,7 @@ void gemm(cvsadc_ctx* c, int prec, int M, int N, int K, double alpha, View A,
       if (ns)
         zgemm_slice(c->stream, ns, M, N, K, alpha, a, b, beta, cc, c->s_tc.p,
                     need, c->s_kpart.c(), c->s_kpart.bytes / sizeof(cplx),
-                    c->err.as<int>(), bc);
+                    c->err.as<int>(), bc, ac);
       else
         zgemm_tc(c->stream, 3, M, N, K, alpha, a, b, beta, cc, c->s_tc.p, need,
                  c->s_kpart.c(), c->s_kpart.bytes / sizeof(cplx),
@@ -643,7 +648,7 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
     const View s1rows = rows2(view(sig, 0, 1), N, v, nc);
     gemm(c, prec, v, g * nc, (int)vL, -1.0,
          cols2(view(B + (int64_t)o * n + o, n, 0), nn, 1, v), view(S, 1, vL),
-         0.0, trans(s1rows));
+         0.0, trans(s1rows), 1, false, true);
     // the <Kb||Ij> part: sigma1[K][c] += sum_{Ijb} y_{Ijcb} conj(h[K][b][I][j]),
     // rows (q, c), columns K
     const View s1t = rows2(view(sig, 0, v), N, 1, v);  // ((q,c), K)
@@ -656,7 +661,7 @@ void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
   // Y^T[(a,P)][(q,I)] = sum_c B^P_ac x_Ic (the long side (a, P) as rows)
   gemm(c, prec, (int)vL, g * nc, v, 1.0,
        rows2(view(B + (int64_t)o * n + o, 0, 1), n, nn, L),
-       trans(rows2(view(x, 0, 1), N, v, nc)), 0.0, trans(view(Y, vL, 1)));
+       trans(rows2(view(x, 0, 1), N, v, nc)), 0.0, trans(view(Y, vL, 1)), 1, false, true);
   // G[q][(I,a)][(j,b)] = sum_P Y B^P_{bj} (the <ab||cj> part of M21 x1; the
   // <Kb||Ij> part is added while packing)
   gemm(c, prec, (int)(g * N1), (int)wv, L, 1.0, view(Y, L, 1),
@@ -2790,14 +2795,16 @@ double estimate_bytes(const cvsadc_params* p) {
     b += w;
   }
   b += (double)(8 << 20) * z + 1024;        // split-K scratch, error flag
-  // cached B^P slice packs: the sigma products with N = v L and K = v L
-  // and the preconditioner's (aj|bc) product, 8 npairs v^2 L bytes each
+  // cached slice packs of B^P views (at most min(35 % of free, 64 GB)): the
+  // B operands of the sigma's S and G products, the A operands of its
+  // sigma1^T and Y^T products, and the preconditioner's (aj|bc) product
   {
     const double pairs = (p->precision == CVSADC_FP64_SLICE7 || needs_refine(p->precision))
                              ? 10.0 + 28.0 : 10.0;
     double cb = schur_on ? 8.0 * 10.0 * v * v * L : 0.0;
     if (p->precision != CVSADC_FP64) cb += 2.0 * 8.0 * pairs * v * v * L;
-    b += std::min(48e9, cb);
+    if (p->precision != CVSADC_FP64) cb += 32.0 * v * v * L;
+    b += std::min(64e9, cb);
   }
   // Schur-complement preconditioner (when the singles space allows it)
   if (N1 <= 4096 && !(p->flags & CVSADC_FLAG_DIAG_PRECOND)) {
