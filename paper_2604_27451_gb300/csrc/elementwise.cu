@@ -254,53 +254,6 @@ __global__ void unpack_kernel(const cplx* __restrict__ x2, int nc, int nw,
   }
 }
 
-// one block per (I, j, a) row of the packed doubles
-// sigma2 = -(G_{Ia,jb} - G_{Ib,ja}) + sum_K (x_Ka h_KbIj - x_Kb h_KaIj)
-//          + M22 x2, packed over a < b (x2 may be NULL: no M22 term; h may be
-// NULL: no h term); h[K][b][I][j] = <Kb||Ij>, x1 the singles [K][a]
-__global__ void sigma2_kernel(const cplx* __restrict__ G,
-                              const cplx* __restrict__ x2,
-                              const cplx* __restrict__ x1,
-                              const cplx* __restrict__ h,
-                              const double* __restrict__ eps, int nc, int nw,
-                              int nv, cplx* __restrict__ s2) {
-  const int64_t npair = (int64_t)nv * (nv - 1) / 2;
-  const int o = nc + nw;
-  const int64_t nrows = (int64_t)nc * nw * nv;
-  for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
-    int a = row % nv;
-    int64_t r = row / nv;
-    int j = r % nw;
-    int I = r / nw;
-    int64_t base = ((int64_t)I * nw + j) * npair + pair_index(a, a + 1, nv) - (a + 1);
-    double e0 = eps[o + a] - eps[I] - eps[nc + j];
-    const cplx* Ga = G + (((int64_t)I * nv + a) * nw + j) * nv;
-    for (int b = a + 1 + threadIdx.x; b < nv; b += blockDim.x) {
-      cplx g1 = Ga[b];
-      cplx g2 = G[(((int64_t)I * nv + b) * nw + j) * nv + a];
-      int64_t d = base + b;
-      cplx out = csub(g2, g1);
-      if (h) {
-        const int64_t hs = (int64_t)nv * nc * nw;  // stride of K in h
-        const int64_t hb = (int64_t)I * nw + j;
-        for (int K = 0; K < nc; ++K) {
-          const cplx xa = x1[(int64_t)K * nv + a], xb = x1[(int64_t)K * nv + b];
-          const cplx hkb = h[K * hs + (int64_t)b * nc * nw + hb];
-          const cplx hka = h[K * hs + (int64_t)a * nc * nw + hb];
-          out = cadd(out, csub(cmul(xa, hkb), cmul(xb, hka)));
-        }
-      }
-      if (x2) {  // without x2: the coupling M21 x1 alone
-        cplx x = x2[d];
-        double m22 = e0 + eps[o + b];
-        out.x += m22 * x.x;
-        out.y += m22 * x.y;
-      }
-      s2[d] = out;
-    }
-  }
-}
-
 // F[I][j][a][b] = -(A[a][b] - A[b][a]) + T[a][b], A and T as [I][j][a][b]
 __global__ void pack_moment_kernel(const cplx* __restrict__ A,
                                    const cplx* __restrict__ T, int nc, int nw,
@@ -434,7 +387,10 @@ struct Ar64 {
 static_assert(sizeof(ArDF::E) == sizeof(cplx) && sizeof(Ar64::E) == sizeof(cplx),
               "staged elements are 16 bytes under both policies");
 
-// The same as sigma2_kernel, tiled: one CTA per (I, j) and pair of 32 x 32
+// sigma2 = -(G_{Ia,jb} - G_{Ib,ja}) + sum_K (x_Ka h_KbIj - x_Kb h_KaIj)
+// + M22 x2, packed over a < b (x2 may be NULL: no M22 term; h may be NULL:
+// no h term); h[K][b][I][j] = <Kb||Ij>, x1 the singles [K][a].  Tiled: one
+// CTA per (I, j) and pair of 32 x 32
 // tiles (a-tile ta <= b-tile tb).  G[I][a][j][b] and G[I][b][j][a] of the
 // two tiles are staged in shared memory with coalesced row reads, so the
 // transposed element is read from shared memory; x1[K][a], x1[K][b] and
