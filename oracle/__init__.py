@@ -21,9 +21,9 @@ Modules:
                    the explicit matrix (CPU, complex128), pinned by central
                    differences of ``adc2`` eigenvalues.
 
-Parity status of each function is stated in its docstring.  One gap is
-declared here: the second-order singles part of the modified transition
-moments, F^(2)_S, is not implemented; oscillator strengths are "through
-first order" (F^(0) + F^(1)), and both F^(0) and F^(1) are pinned by the
-brute-force ISR.
+Parity status of each function is stated in its docstring.  The modified
+transition moments are pinned by the brute-force ISR through second order:
+F^(0) and F^(1) for all CVS rows, and the second-order singles term F^(2)_S
+(``adc2.transition_moments(..., order=2)``) together with the second-order
+ground-state amplitudes it is built from.
 """

@@ -40,8 +40,23 @@ ISR formulation"), through first order (pinned by the same brute force):
   F_{Ijab} = - sum_c (d_ac t^{cb}_{Ij} - d_bc t^{ca}_{Ij})
              + sum_k (d_kI t^{ab}_{kj} - d_kj t^{ab}_{kI})
 
-T_n = X_n^H F, f_n = 2/3 omega_n |T_n|^2.  The second-order singles term
-F^(2) is not implemented (declared in ``oracle/__init__.py``).
+and, with ``order=2``, the second-order singles term (the full ISR's
+singles class, CVS as a projection; s and u the second-order ground-state
+amplitudes of ``oracle.mp2``):
+
+  F^(2)_{Ia} = sum_c d_ac s_Ic - sum_k d_kI s_ka + sum_{kc} d_kc u^{ac}_{Ik}
+               - 1/4 sum_k d_ak H_kI + 1/2 sum_{ld} w_ld t^{ad}_{Il}
+               - 1/4 sum_c d_cI P_ca
+  H_kI = sum_{lde} conj(t^{de}_{kl}) t^{de}_{Il},
+  P_ca = sum_{lmd} conj(t^{cd}_{lm}) t^{ad}_{lm},
+  w_ld = sum_{ck} d_ck conj(t^{cd}_{kl}).
+
+The last three terms are half of sum_{ck} d_ck (<Psi1|a_I^+ a_a a_c^+ a_k|Psi1>
+- <Psi1|Psi1> d_Ik d_ac): the ground state's own second-order pieces carry
+that expectation value whole, and the S^{-1/2} of the singles class takes
+back half of it.  Pinned by the brute-force ISR at lambda^2.
+
+T_n = X_n^H F, f_n = 2/3 omega_n |T_n|^2.
 """
 
 from __future__ import annotations
@@ -54,7 +69,7 @@ import scipy.optimize
 import scipy.sparse.linalg
 
 from .integrals import antisym
-from .mp2 import t2_amplitudes
+from .mp2 import second_order_doubles, second_order_singles, t2_amplitudes
 
 
 # --------------------------------------------------------------------------
@@ -251,16 +266,47 @@ class Sigma:
 # transition moments and oscillator strengths
 # --------------------------------------------------------------------------
 
-def transition_moments(eps, B, dip, ncore, nval, nvirt, t2=None):
-    """F[x] = [F_S (N1), F_D (N2)] for each Cartesian component x, through
-    first order."""
+def singles_moments_second_order(eps, B, dip, ncore, nval, nvirt, t2=None):
+    """F^(2)_{Ia} for each Cartesian component, as [x, I, a] (module
+    docstring)."""
     C, W, O, V = _idx(ncore, nval, nvirt)
     if t2 is None:
         t2 = t2_amplitudes(eps, B, ncore, nval, nvirt)
+    s = second_order_singles(eps, B, ncore, nval, nvirt, t2=t2)  # [k, c]
+    u = second_order_doubles(eps, B, ncore, nval, nvirt, t2=t2, rows=C)  # [I, k, a, c]
+    tI = t2[C]  # [I, l, a, d]
+    H = np.einsum("klde,Ilde->kI", np.conj(t2), tI, optimize=True)
+    P = np.einsum("lmcd,lmad->ca", np.conj(t2), t2, optimize=True)
+    out = []
+    for x in range(dip.shape[0]):
+        d = dip[x]
+        dvv, doo, dov, dvo = (d[np.ix_(V, V)], d[np.ix_(O, O)], d[np.ix_(O, V)],
+                              d[np.ix_(V, O)])
+        w = np.einsum("ck,klcd->ld", dvo, np.conj(t2), optimize=True)
+        f2 = (np.einsum("ac,Ic->Ia", dvv, s[C])
+              - np.einsum("kI,ka->Ia", doo[:, C], s)
+              + np.einsum("kc,Ikac->Ia", dov, u, optimize=True)
+              - 0.25 * np.einsum("ak,kI->Ia", dvo, H)
+              + 0.5 * np.einsum("ld,Ilad->Ia", w, tI)
+              - 0.25 * np.einsum("cI,ca->Ia", dvo[:, C], P))
+        out.append(f2)
+    return np.stack(out)
+
+
+def transition_moments(eps, B, dip, ncore, nval, nvirt, t2=None, order=1):
+    """F[x] = [F_S (N1), F_D (N2)] for each Cartesian component x, through
+    first order; order=2 adds the second-order singles term."""
+    C, W, O, V = _idx(ncore, nval, nvirt)
+    if t2 is None:
+        t2 = t2_amplitudes(eps, B, ncore, nval, nvirt)
+    f2 = (singles_moments_second_order(eps, B, dip, ncore, nval, nvirt, t2=t2)
+          if order >= 2 else None)
     out = []
     for x in range(dip.shape[0]):
         d = dip[x]
         fs = d[np.ix_(V, C)].T + np.einsum("kc,Ikac->Ia", d[np.ix_(O, V)], t2[C])
+        if f2 is not None:
+            fs = fs + f2[x]
         dvv = d[np.ix_(V, V)]
         doo = d[np.ix_(O, O)]
         tcw = t2[C][:, W]  # t^{ab}_{Ij}

@@ -18,7 +18,9 @@ Diagrammatic Construction Method" defines them:
   overlap equations);
 * M_IJ = <Psi~_I|H - E_0|Psi~_J> (the secular-matrix equation), and the
   modified transition moments F_I = <Psi~_I|D|Psi_0> (section "Properties in
-  ISR formulation").
+  ISR formulation");
+* the exact ground state's own expansion (its determinant amplitudes and
+  one-particle density), for the Rayleigh-Schrodinger pieces.
 
 The perturbation expansion M = M(0) + M(1) + M(2) + ... (Eq. 12) is then
 read off as the Taylor coefficients of M(lambda) at lambda = 0, obtained by a
@@ -316,6 +318,36 @@ class ISR:
         Vm = np.vander(lams / h, deg + 1, increasing=True)
         c = (np.linalg.pinv(Vm) @ np.stack(gs).reshape(npts, -1)) * (h ** -np.arange(deg + 1))[:, None]
         return c[: order + 1].reshape(order + 1, n, n)
+
+    def ground_state_taylor(self, order: int = 2, h: float = 0.02, deg: int = 8,
+                            npts: int = 17):
+        """Taylor coefficients [0..order] at lambda = 0 of the exact ground
+        state Psi_0(lambda) of H(lambda), normalised with <Phi_0|Psi_0> real
+        and positive, as vectors over the determinants (the same Chebyshev
+        least-squares fit as ``taylor``).  Its lambda^1 and lambda^2
+        coefficients on a determinant are the first- and second-order
+        amplitudes of Rayleigh-Schrodinger theory (the normalisation enters
+        only the reference coefficient at lambda^2)."""
+        ref = self.space.index[self.space.ref]
+        k = np.arange(npts)
+        lams = h * np.cos((2 * k + 1) * np.pi / (2 * npts))
+        vecs = []
+        for lam in lams:
+            _, U = np.linalg.eigh(np.diag(self.h0) + lam * self.V)
+            p = U[:, 0]
+            vecs.append(p * (np.conj(p[ref]) / abs(p[ref])))
+        Vm = np.vander(lams / h, deg + 1, increasing=True)
+        c = (np.linalg.pinv(Vm) @ np.stack(vecs)) * (h ** -np.arange(deg + 1))[:, None]
+        return c[: order + 1]
+
+    def amplitude(self, coeff: np.ndarray, creators, annihilators) -> complex:
+        """<Phi|coeff> for Phi = a^+_{c1} a^+_{c2} .. a_{k2} a_{k1} Phi_0, the
+        determinant made by the given creators (left to right) and
+        annihilators (applied first, in reversed order)."""
+        ops = [(1, c) for c in creators] + [(0, k) for k in reversed(annihilators)]
+        ref = np.zeros(self.space.dim, dtype=np.complex128)
+        ref[self.space.index[self.space.ref]] = 1.0
+        return np.vdot(self.space.act(self.space.operator(ops), ref), coeff)
 
     def rspt_e2(self) -> float:
         """Second-order Rayleigh-Schrodinger energy from the determinant

@@ -192,6 +192,66 @@ def test_isr_pins_transition_moments(tiny):
     assert np.abs(cF[1]).max() > 1e-3 * np.abs(cF[0]).max()
 
 
+def test_isr_pins_second_order_amplitudes(tiny):
+    """The lambda^1 and lambda^2 amplitudes of the exact ground state on
+    singles and doubles determinants are t2 and the second-order s and u
+    (Rayleigh-Schrodinger with the MP partitioning)."""
+    inst, isr, cM, cF, cE = tiny
+    nc, nw, nv = inst.ncore, inst.nval, inst.nvirt
+    o = nc + nw
+    c = isr.ground_state_taylor()
+    t2 = mp2.t2_amplitudes(inst.eps, inst.B, nc, nw, nv)
+    s = mp2.second_order_singles(inst.eps, inst.B, nc, nw, nv, t2=t2)
+    u = mp2.second_order_doubles(inst.eps, inst.B, nc, nw, nv, t2=t2)
+    s_ex = np.array([[isr.amplitude(c[2], [o + a], [k]) for a in range(nv)] for k in range(o)])
+    assert np.abs(s - s_ex).max() < 1e-8 * np.abs(s_ex).max()
+    assert np.abs(s_ex).max() > 1e-4
+    err_u, err_t, mx = 0.0, 0.0, 0.0
+    for k, l in itertools.combinations(range(o), 2):
+        for a, b in itertools.combinations(range(nv), 2):
+            ex2 = isr.amplitude(c[2], [o + a, o + b], [k, l])
+            ex1 = isr.amplitude(c[1], [o + a, o + b], [k, l])
+            err_u = max(err_u, abs(u[k, l, a, b] - ex2))
+            err_t = max(err_t, abs(t2[k, l, a, b] - ex1))
+            mx = max(mx, abs(ex2))
+    assert err_t < 1e-10
+    assert err_u < 1e-8 * mx and mx > 1e-4
+    # the core rows alone, as the moments use them
+    uc = mp2.second_order_doubles(inst.eps, inst.B, nc, nw, nv, t2=t2, rows=slice(0, nc))
+    assert np.abs(uc - u[:nc]).max() < 1e-14
+
+
+def test_isr_pins_second_order_singles_moments(tiny):
+    """F^(2)_S = the lambda^2 coefficient of the brute-force ISR's singles
+    moments (section "Properties in ISR formulation"), every term of it
+    carrying weight."""
+    inst, isr, cM, cF, cE = tiny
+    nc, nw, nv = inst.ncore, inst.nval, inst.nvirt
+    N1 = nc * nv
+    f2 = adc2.singles_moments_second_order(inst.eps, inst.B, inst.dip, nc, nw, nv)
+    ref = cF[2][:, :N1].reshape(f2.shape)
+    scale = np.abs(ref).max()
+    assert np.abs(f2 - ref).max() < 1e-8 * scale
+    F = adc2.transition_moments(inst.eps, inst.B, inst.dip, nc, nw, nv, order=2)
+    assert np.abs(F - (cF[0] + cF[1] + np.concatenate(
+        [cF[2][:, :N1], np.zeros_like(cF[2][:, N1:])], axis=1))).max() < 1e-8 * scale
+    # each of the six terms alone moves the result far beyond the tolerance
+    C, O, V = np.arange(nc), np.arange(nc + nw), np.arange(nc + nw, nc + nw + nv)
+    t2 = mp2.t2_amplitudes(inst.eps, inst.B, nc, nw, nv)
+    s = mp2.second_order_singles(inst.eps, inst.B, nc, nw, nv, t2=t2)
+    u = mp2.second_order_doubles(inst.eps, inst.B, nc, nw, nv, t2=t2, rows=C)
+    d = inst.dip[0]
+    dvv, doo, dov, dvo = d[np.ix_(V, V)], d[np.ix_(O, O)], d[np.ix_(O, V)], d[np.ix_(V, O)]
+    H = np.einsum("klde,Ilde->kI", np.conj(t2), t2[C])
+    P = np.einsum("lmcd,lmad->ca", np.conj(t2), t2)
+    w = np.einsum("ck,klcd->ld", dvo, np.conj(t2))
+    terms = [np.einsum("ac,Ic->Ia", dvv, s[C]), np.einsum("kI,ka->Ia", doo[:, C], s),
+             np.einsum("kc,Ikac->Ia", dov, u), np.einsum("ak,kI->Ia", dvo, H),
+             np.einsum("ld,Ilad->Ia", w, t2[C]), np.einsum("cI,ca->Ia", dvo[:, C], P)]
+    for term in terms:
+        assert np.abs(term).max() > 1e-4 * scale
+
+
 # ------------------------------------------------ T4 Hermiticity and sigma
 
 def test_hermitian_and_sigma_equals_dense():
