@@ -1,10 +1,11 @@
 """The synthetic inputs follow their stated recipes (no method arithmetic
-here): Hermitian Cholesky vectors and dipoles, the energy partitions, and
-the ragged batch of 48 instances."""
+here): Hermitian Cholesky vectors and dipoles, the energy partitions, the
+stated and the physical Cholesky scales, and the ragged batch of 48
+instances."""
 
 import numpy as np
 
-from synth import batched_shapes, make_instance
+from synth import batched_shapes, make_instance, physical_scale
 
 
 def test_instance_structure():
@@ -31,3 +32,17 @@ def test_batched_recipe():
         assert s["nval"] % 2 == 0 and 20 <= s["nval"] <= 80
         assert 100 <= s["nvirt"] <= 400 and s["naux"] == 5 * s["nvirt"]
     assert len({(s["nval"], s["nvirt"]) for s in sh}) > 40  # ragged
+
+
+def test_cholesky_scales():
+    # the stated scale: B^0 entries are N(0,1) (+ i N(0,1)) times 0.3
+    a = make_instance(2, 4, 10, 3, seed=1)
+    off = a.B[0][np.triu_indices(a.B.shape[1], 1)]
+    assert 0.2 < np.std(off.real) / 0.3 < 5.0
+    # the physical scale 0.34 (nval nvirt^2)^(-1/4): the same draws, scaled
+    sc = physical_scale(4, 10)
+    assert abs(sc - 0.34 * (4 * 100) ** -0.25) < 1e-15
+    assert abs(physical_scale(0, 10) - 0.34 * 100 ** -0.25) < 1e-15
+    b = make_instance(2, 4, 10, 3, seed=1, scale=sc)
+    assert np.array_equal(a.eps, b.eps)
+    assert np.allclose(b.B, a.B * (sc / 0.3), rtol=1e-15, atol=0)
