@@ -232,9 +232,10 @@ int cvsadc_solve_batched(cvsadc_ctx* ctx, int32_t ninst,
                          int32_t lanes);
 
 /* Upper estimate of the device bytes one cvsadc_solve of `params` holds at
- * its peak (inputs, t2 and <ab||ij>, M11, the Davidson subspace, the sigma
- * intermediates of the largest block, the tensor-core workspace), computed
- * on the host without a GPU.  Errors: EINVAL for invalid params. */
+ * its peak (inputs, the t2 / <ab||ij> band buffers, M11, the Davidson
+ * subspace, the sigma intermediates of the largest block, the tensor-core
+ * workspace and the kept operand packs), computed on the host without a
+ * GPU.  Errors: EINVAL for invalid params. */
 int cvsadc_estimate_bytes(const cvsadc_params* params, int64_t* bytes);
 
 /* Device bytes the buffers of ctx hold now (they persist between calls and
@@ -289,7 +290,10 @@ int cvsadc_get_moments(cvsadc_ctx* ctx, int32_t flags, void* F);
 /* sigma = M x for nvec CVS-packed vectors x [nvec][N] complex, written to
  * sigma [nvec][N].  precision: any CVSADC_FP64 / CVSADC_MIXED_* (the
  * couplings M12 and M21 are contracted through B^P; M22 is applied on the
- * fly; M11 x1 is a dense product). */
+ * fly; M11 x1 is a dense product).  With the tensor-core precisions the
+ * packed slices of the products' operands that are fixed views of B^P are
+ * kept in ctx after the first call (at most min(35 % of the free device
+ * memory, 64 GB)); preparing another problem releases them. */
 int cvsadc_sigma(cvsadc_ctx* ctx, int32_t precision, int32_t flags,
                  const void* x, void* sigma, int32_t nvec);
 
