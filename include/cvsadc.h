@@ -232,10 +232,14 @@ int cvsadc_solve_batched(cvsadc_ctx* ctx, int32_t ninst,
                          int32_t lanes);
 
 /* Upper estimate of the device bytes one cvsadc_solve of `params` holds at
- * its peak (inputs, the t2 / <ab||ij> band buffers, M11, the Davidson
- * subspace, the sigma intermediates of the largest block, the tensor-core
- * workspace and the kept operand packs), computed on the host without a
- * GPU.  Errors: EINVAL for invalid params. */
+ * its peak (inputs, the t2 / <ab||ij> band buffers, M11, the eigensolver's
+ * vectors, the sigma intermediates of the largest group, the
+ * preconditioner, the tensor-core workspace and the kept operand packs),
+ * computed on the host without a GPU.  Without CVSADC_FLAG_FOLDED it prices
+ * the full-space Davidson subspace; the solve itself switches to the
+ * doubles-folded solver when that subspace does not fit on the device, and
+ * with the flag set the estimate prices that solver.  Errors: EINVAL for
+ * invalid params. */
 int cvsadc_estimate_bytes(const cvsadc_params* params, int64_t* bytes);
 
 /* Device bytes the buffers of ctx hold now (they persist between calls and

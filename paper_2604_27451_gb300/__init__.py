@@ -399,12 +399,14 @@ class Context:
 
 
 def estimate_bytes(ncore, nval, nvirt, naux, nroots=4, precision="fp64", tau=0.0,
-                   max_subspace=0):
+                   max_subspace=0, solver="auto"):
     """cvsadc_estimate_bytes: device bytes one solve holds at its peak (host
-    arithmetic, no GPU needed)."""
+    arithmetic, no GPU needed); solver="folded" prices the doubles-folded
+    solver."""
     lib = _lib.load()
     p = Context.params(ncore, nval, nvirt, naux, nroots, precision, tau,
-                       max_subspace=max_subspace)
+                       max_subspace=max_subspace,
+                       flags=CVSADC_FLAG_FOLDED if solver == "folded" else 0)
     out = ctypes.c_int64()
     rc = lib.cvsadc_estimate_bytes(ctypes.byref(p), ctypes.byref(out))
     if rc != 0:

@@ -617,6 +617,8 @@ void build_h(cvsadc_ctx* c, int prec) {
 // M21 x1 (no M22 term, singles part untouched).  SIG_ADJ: only the singles
 // part, sigma1 = M12 x2 (no M11 term, doubles part untouched).
 enum { SIG_FULL = 0, SIG_FWD = 1, SIG_ADJ = 2 };
+// bytes of sigma intermediates (unpacked doubles, G, S, Y) one group holds
+constexpr double SIGMA_BUDGET = 48e9;
 void sigma_group(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int g,
                  int mode = SIG_FULL) {
   const int nc = c->ncore, nw = c->nval, v = c->nvirt, o = c->o, n = c->n,
@@ -682,8 +684,7 @@ void sigma_impl(cvsadc_ctx* c, int prec, const cplx* x, cplx* sig, int nvec,
                 int mode = SIG_FULL) {
   const int64_t N1 = c->N1, wv = (int64_t)c->nval * c->nvirt, L = c->naux;
   const double per_vec = (2.0 * N1 * wv + 2.0 * N1 * L + 2.0 * wv * L) * sizeof(cplx);
-  const double budget = 48e9;
-  int g = (int)std::max(1.0, std::min((double)nvec, budget / per_vec));
+  int g = (int)std::max(1.0, std::min((double)nvec, SIGMA_BUDGET / per_vec));
   for (int q0 = 0; q0 < nvec; q0 += g) {
     const int gg = std::min(g, nvec - q0);
     sigma_group(c, prec, x + q0 * c->N, sig + q0 * c->N, gg, mode);
@@ -2234,7 +2235,7 @@ bool full_space_fits(cvsadc_ctx* c, int k, int max_sub) {
     (void)cudaGetLastError();
     return true;
   }
-  return need + (double)c->held_bytes() * 0.0 < 0.85 * (double)free_b;
+  return need < 0.85 * (double)free_b;
 }
 
 // The doubles-folded solver behind cvsadc_davidson: roots, and (when asked)
@@ -2730,11 +2731,14 @@ int guarded(cvsadc_ctx* c, F&& f) {
 namespace {
 
 // Device bytes one solve of `p` holds at its peak: inputs, the t2 band
-// buffers, the moment accumulators, M11 and its build scratch, the Davidson subspace and
-// block vectors, the sigma intermediates of its largest block (the initial
-// guesses), the tensor-core packing workspace of the largest contraction
-// and the split-K scratch.  Host arithmetic only; used to admit instances
-// of a batch to the GPU and offered to callers that size their own memory.
+// buffers, the moment accumulators, M11 and its build scratch, the
+// eigensolver's vectors (the full-space Davidson subspace and block, or
+// with CVSADC_FLAG_FOLDED the folded solver's singles-space vectors and
+// the lift of the eigenvectors), the sigma intermediates of its largest
+// group, the preconditioner, the tensor-core packing workspace of the
+// largest contraction, the kept operand packs and the split-K scratch.
+// Host arithmetic only; used to admit instances of a batch to the GPU and
+// offered to callers that size their own memory.
 double estimate_bytes(const cvsadc_params* p) {
   const double z = sizeof(cplx);
   const double nc = p->ncore, nw = p->nval, v = p->nvirt, L = p->naux;
@@ -2746,8 +2750,14 @@ double estimate_bytes(const cvsadc_params* p) {
   const int ms = std::max(msub, 2 * k + 2);
   const int nkeep = std::max(k, std::min(ms / 3, ms - 2 * k));
   const bool schur_on = N1 <= 4096 && !(p->flags & CVSADC_FLAG_DIAG_PRECOND);
+  const bool folded = (p->flags & CVSADC_FLAG_FOLDED) != 0;
   double g = std::min(64, std::max(k, std::min(2 * k, ms / 2)));
   if (schur_on) g = std::max(g, std::min<double>(SCHUR_P, N1));
+  // sigma_impl runs at most as many vectors at once as fit its budget
+  {
+    const double per_vec = (2.0 * N1 * wv + 2.0 * N1 * L + 2.0 * wv * L) * z;
+    g = std::max(1.0, std::min(g, std::floor(SIGMA_BUDGET / per_vec)));
+  }
   double b = 8 * n + z * L * n * n;
   b += 3 * z * n * n;                       // dipoles
   // t2 bands: the in-place (ai|bj) / <ab||ij> block and the t2 block
@@ -2760,8 +2770,20 @@ double estimate_bytes(const cvsadc_params* p) {
                  z * g * N1 * wv, 2 * z * nc * nw * v * v});  // s_big2
   b += z * N1 * N1 + 8 * N;                 // M11, diagonal
   b += 2 * z * g * N1 * L + 2 * z * g * wv * L;  // S, Y, R, V
-  b += z * N * (2.0 * ms + 2.0 * nkeep + k);  // Davidson V, W, X, AX, T
+  if (folded) {
+    // the folded solver: singles-space V, B, R, D, M11 V and block scratch,
+    // and the lift of the full eigenvectors (groups within 24 GB)
+    const double fms = std::min(128, std::max(p->max_subspace, 3 * k + 2));
+    b += z * N1 * (5.0 * fms + 9.0 * k);
+    b += std::min(24e9, 2.0 * z * N * k);
+  } else {
+    b += z * N * (2.0 * ms + 2.0 * nkeep + k);  // Davidson V, W, X, AX, T
+  }
   b += z * (double)ms * ms * 320 + 1e6;     // subspace matrices, partials
+  if (N1 > SCHUR_FULL_MAX && !(p->flags & CVSADC_FLAG_DIAG_PRECOND))
+    // the large-space preconditioner: partial eigenbasis, j-chunk buffers,
+    // S(theta) and its cross-term blocks
+    b += z * N1 * SCHUR_PL * 4.0 + 6.5e9 + 2.0 * z * N1 * N1 + z * v * v * nc * nc;
   b += 3 * z * N;                           // moments
   if (p->precision != CVSADC_FP64 || schur_on) {
     const int ns = p->precision == CVSADC_MIXED_SLICE4 ? 4

@@ -85,6 +85,23 @@ def test_estimate_bytes_without_gpu():
         est(0, nw, nv, L)
 
 
+def test_estimate_bytes_large_shape_without_gpu():
+    """The large shape (12/120/600/3000, 16 roots): a full-space subspace of
+    4.14 GB vectors does not fit one GPU, the doubles-folded solver does;
+    its estimate still covers B^P, the t2 bands and the sigma
+    intermediates of one vector."""
+    import paper_2604_27451_gb300 as pkg
+
+    nc, nw, nv, L, k = 12, 120, 600, 3000, 16
+    n = nc + nw + nv
+    full = pkg.estimate_bytes(nc, nw, nv, L, nroots=k, precision="slice4")
+    fold = pkg.estimate_bytes(nc, nw, nv, L, nroots=k, precision="slice4", solver="folded")
+    assert full > 1e12
+    assert fold < 284208 * 2**20  # one GB300's HBM (nvidia-smi total)
+    floor = 16 * L * n * n + 16e9 + 2 * 16 * nc * nv * nw * nv
+    assert fold > floor
+
+
 def test_batched_and_bytes_reject_null_without_gpu():
     from paper_2604_27451_gb300 import _lib
 
