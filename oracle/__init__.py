@@ -16,6 +16,8 @@ Modules:
                    independent pin of the ``adc2`` element formulas;
 * ``spectrum``  -- Lorentzian-broadened spectrum from roots and oscillator
                    strengths;
+* ``cisd``      -- CIS(D) energies and the frozen-natural-spinor correction
+                   of Eqs. 21-22;
 * ``grad``      -- the gradient of a sum of roots with respect to the spinor
                    energies and the Cholesky vectors, by torch autograd of
                    the explicit matrix (CPU, complex128), pinned by central

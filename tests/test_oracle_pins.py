@@ -14,7 +14,7 @@ import itertools
 import numpy as np
 import pytest
 
-from oracle import adc2, fns, mp2, spectrum
+from oracle import adc2, cisd, fns, mp2, spectrum
 from oracle.fci import DetSpace, ISR, apply_string, full_antisym_integrals
 from oracle.integrals import antisym
 from synth import make_instance, make_kramers_instance, make_spinfree_instance
@@ -250,6 +250,65 @@ def test_isr_pins_second_order_singles_moments(tiny):
              np.einsum("ld,Ilad->Ia", w, t2[C]), np.einsum("cI,ca->Ia", dvo[:, C], P)]
     for term in terms:
         assert np.abs(term).max() > 1e-4 * scale
+
+
+# --------------------------------------------- CIS(D) and Eqs. 21-22 (N1)
+
+CISD = dict(ncore=2, nval=3, nvirt=8, naux=14, seed=5, scale=0.1)
+
+
+def _cisd_instance():
+    c = CISD
+    return make_instance(c["ncore"], c["nval"], c["nvirt"], c["naux"], seed=c["seed"],
+                         scale=c["scale"])
+
+
+def test_cisd_is_the_second_order_estimate_of_adc2():
+    """omega_CIS(D) - omega_CIS is the lambda^2 coefficient of the lowest
+    eigenvalues of [[M_CIS + lambda^2 M11^(2), lambda M12], [lambda M21,
+    M22]] (exact eigenvalues of the scaled matrix, Chebyshev fit); the
+    explicit u^{ab}_{Ij} gives the same doubles term as the folded form."""
+    inst = _cisd_instance()
+    nc, nw, nv = CISD["ncore"], CISD["nval"], CISD["nvirt"]
+    k = 3
+    w, wd, b = cisd.cisd_energies(inst.eps, inst.B, nc, nw, nv, k)
+    A = cisd.cis_block(inst.eps, inst.B, nc, nw, nv)
+    M2 = adc2.m11(inst.eps, inst.B, nc, nw, nv) - A
+    M21 = adc2.m21(inst.eps, inst.B, nc, nw, nv)
+    d22 = adc2.m22(inst.eps, nc, nw, nv)
+    h, npts = 0.05, 17
+    lams = h * np.cos((2 * np.arange(npts) + 1) * np.pi / (2 * npts))
+    vals = []
+    for lam in lams:
+        M = np.block([[A + lam ** 2 * M2, lam * M21.conj().T],
+                      [lam * M21, np.diag(d22).astype(complex)]])
+        vals.append(np.linalg.eigvalsh(M)[:k])
+    Vm = np.vander(lams / h, 9, increasing=True)
+    c = (np.linalg.pinv(Vm) @ np.array(vals)) * (h ** -np.arange(9))[:, None]
+    assert np.abs(c[0] - w).max() < 1e-10
+    assert np.abs(c[2] - (wd - w)).max() < 1e-7 * np.abs(wd - w).max()
+    assert np.abs(wd - w).min() > 1e-2
+    M11b = np.einsum("ki,ij,kj->k", np.conj(b), M2, b).real
+    for q in range(k):
+        eu = cisd.doubles_term_explicit(inst.eps, inst.B, nc, nw, nv, w[q], b[q])
+        assert abs(eu - (wd[q] - w[q] - M11b[q])) < 1e-12 * abs(eu)
+
+
+def test_fns_correction_eqs_21_22():
+    """Keeping every virtual leaves dE = 0; with two of eight natural
+    virtuals dropped, the corrected roots (Eq. 22) are closer to the
+    canonical CVS-ADC(2) roots than the uncorrected ones."""
+    inst = _cisd_instance()
+    nc, nw, nv = CISD["ncore"], CISD["nval"], CISD["nvirt"]
+    k = 3
+    dE, w_fns, w_corr = cisd.fns_correction(inst.eps, inst.B, nc, nw, nv, k, 1e-30)
+    assert np.abs(dE).max() < 1e-12
+    n, _, _ = fns.natural_spinors(inst.eps, inst.B, nc, nw, nv, 0.0)
+    tau = 0.5 * (n[5] + n[6])
+    dE, w_fns, w_corr = cisd.fns_correction(inst.eps, inst.B, nc, nw, nv, k, tau)
+    w_can = np.linalg.eigvalsh(adc2.adc_matrix(inst.eps, inst.B, nc, nw, nv))[:k]
+    assert np.all(np.abs(w_corr - w_can) < np.abs(w_fns - w_can))
+    assert np.abs(w_fns - w_can).min() > 1e-2
 
 
 # ------------------------------------------------ T4 Hermiticity and sigma
