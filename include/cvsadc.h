@@ -81,10 +81,14 @@ extern "C" {
                                   of (row max x column max) */
 #define CVSADC_FP64_SLICE7 3   /* as SLICE4 with seven slices (28 products):
                                   FP64-class accuracy on the tensor cores.
-                                  In all mixed modes the denominators,
-                                  Gram-Schmidt, norms, subspace eigensolve
-                                  and the final residual correction run in
-                                  FP64 */
+                                  In every precision the denominators, the
+                                  subspace eigensolve and the final residual
+                                  correction run in FP64; the Davidson inner
+                                  products, Gram-Schmidt and norms run in
+                                  FP64 for CVSADC_FP64 and FP64_SLICE7 and in
+                                  double-float on the FP32 pipes for the two
+                                  mixed modes (products within ~2^-46 of
+                                  |a||b|, tiles summed in FP64) */
 
 /* ---------------------------------------------------------------- flags */
 #define CVSADC_FLAG_DEVICE_PTRS 1  /* array arguments are device pointers */
@@ -166,7 +170,13 @@ const char* cvsadc_last_error(cvsadc_ctx* ctx);
  * singles space has at most 4096 elements and the lowest root lies below
  * every M22 entry; CVSADC_FLAG_DIAG_PRECOND selects the diagonal
  * preconditioner instead.  The preconditioner changes the iteration, not
- * the converged roots.
+ * the converged roots.  When the full-space Davidson subspace would not fit
+ * on the device, or with CVSADC_FLAG_FOLDED, the doubles-folded solver runs
+ * instead: a Rayleigh-Ritz of M over singles vectors lifted with
+ * (w - M22)^-1 M21 (exact because M22 is diagonal, Eqs. 11-12), which
+ * stores no doubles vector; above 4096 singles its preconditioner is the
+ * lowest 64 eigenpairs of S(theta0).  The full eigenvectors (X) and the
+ * oscillator strengths are rebuilt from the converged singles.
  *   omega : [nroots] out, ascending excitation energies (Eh)
  *   X     : [nroots][N] complex out (CVS packed, in the final basis) or NULL;
  *           written only with CVSADC_FLAG_RETURN_X.  The largest-modulus
