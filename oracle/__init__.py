@@ -18,6 +18,8 @@ Modules:
                    strengths;
 * ``cisd``      -- CIS(D) energies and the frozen-natural-spinor correction
                    of Eqs. 21-22;
+* ``rootsel``   -- canonical CIS guesses mapped into the FNS basis and
+                   root-specific selection of the CVS-ADC(2) roots;
 * ``grad``      -- the gradient of a sum of roots with respect to the spinor
                    energies and the Cholesky vectors, by torch autograd of
                    the explicit matrix (CPU, complex128), pinned by central

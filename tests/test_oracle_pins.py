@@ -14,7 +14,7 @@ import itertools
 import numpy as np
 import pytest
 
-from oracle import adc2, cisd, fns, mp2, spectrum
+from oracle import adc2, cisd, fns, mp2, rootsel, spectrum
 from oracle.fci import DetSpace, ISR, apply_string, full_antisym_integrals
 from oracle.integrals import antisym
 from synth import make_instance, make_kramers_instance, make_spinfree_instance
@@ -309,6 +309,45 @@ def test_fns_correction_eqs_21_22():
     w_can = np.linalg.eigvalsh(adc2.adc_matrix(inst.eps, inst.B, nc, nw, nv))[:k]
     assert np.all(np.abs(w_corr - w_can) < np.abs(w_fns - w_can))
     assert np.abs(w_fns - w_can).min() > 1e-2
+
+
+def test_cis_guesses_map_into_the_fns_basis():
+    """With every virtual kept U is unitary, so the canonical CIS
+    eigenvectors mapped by U^H are CIS eigenvectors of the rotated problem
+    with the same energies (the orientation U instead of U^H fails)."""
+    inst = _cisd_instance()
+    nc, nw, nv = CISD["ncore"], CISD["nval"], CISD["nvirt"]
+    _, U, et = fns.natural_spinors(inst.eps, inst.B, nc, nw, nv, 0.0)
+    e2, B2 = fns.rotate(inst.eps, inst.B, nc, nw, nv, U, et)
+    w, _, _ = cisd.cisd_energies(inst.eps, inst.B, nc, nw, nv, 3)
+    g = rootsel.cis_guesses_in_fns(inst.eps, inst.B, nc, nw, nv, 3, U)
+    A2 = cisd.cis_block(e2, B2, nc, nw, nv)
+    for k in range(3):
+        assert np.linalg.norm(A2 @ g[k] - w[k] * g[k]) < 1e-12
+        assert abs(np.linalg.norm(g[k]) - 1.0) < 1e-12
+
+
+def test_root_following_selects_by_overlap():
+    """Guesses equal to the singles parts of chosen eigenvectors select
+    exactly those eigenpairs, in the guesses' order; following the CIS
+    states in the keep-all FNS basis gives the roots that following them in
+    the canonical basis gives."""
+    inst = _cisd_instance()
+    nc, nw, nv = CISD["ncore"], CISD["nval"], CISD["nvirt"]
+    N1 = nc * nv
+    M = adc2.adc_matrix(inst.eps, inst.B, nc, nw, nv)
+    w, V = np.linalg.eigh(M)
+    pick = [5, 1, 3]
+    g = V[:N1, pick].T
+    g = g / np.linalg.norm(g, axis=1)[:, None]
+    wf, X = rootsel.follow_roots(M, N1, g)
+    assert np.abs(wf - w[pick]).max() < 1e-12
+    for k, j in enumerate(pick):
+        assert abs(abs(np.vdot(X[k], V[:, j])) - 1.0) < 1e-10
+    _, _, b = cisd.cisd_energies(inst.eps, inst.B, nc, nw, nv, 3)
+    w_can, _ = rootsel.follow_roots(M, N1, b)
+    w_fns, _, _ = rootsel.root_specific_fns(inst.eps, inst.B, nc, nw, nv, 3, 0.0)
+    assert np.abs(w_fns - w_can).max() < 1e-10
 
 
 # ------------------------------------------------ T4 Hermiticity and sigma
